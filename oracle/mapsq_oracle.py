@@ -122,7 +122,7 @@ def join_mapreduce(L, R):
     lsel = lrows[value[rs_left]]
     rsel = rrows[value[rs_right]]
     rs = np.concatenate((lsel[:, lk], lsel[:, lrest], rsel[:, rrest]), axis=1)
-    return out_vars, rs.astype(np.uint32).reshape(-1, len(out_vars))
+    return out_vars, rs.astype(np.uint32).reshape(rs_left.shape[0], len(out_vars))
 
 
 def canonical(t):

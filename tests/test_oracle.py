@@ -164,6 +164,8 @@ def test_join_special_cases(join):
     unit = gen.Table.unit(1)
     assert sorted(map(tuple, join(L3, unit)[1].tolist())) == sorted(map(tuple, oracle.as_rows(L3)[1].tolist()))
     assert join(L3, gen.Table.unit(0))[1].shape == (0, 2)
+    assert join(unit, unit)[1].shape == (1, 0)
+    assert join(unit, gen.Table.unit(0))[1].shape == (0, 0)
 
 
 def test_skewed_two_key_closed_form():
