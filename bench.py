@@ -1,0 +1,441 @@
+"""Benchmark of the MapSQ join path on GB300.
+
+Default workload: plain BGP evaluation over a seeded university-shaped graph of
+1e7 triples, 32 star and chain BGPs of 3-6 patterns (one step = every BGP
+evaluated once through ``mapsq_query``: pattern scans, joins, result tables).
+Metric: output bindings/s (one binding = one solution row of a BGP).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload university_bgp|skewed_join|pairwise_uniform]
+
+``--impl reference`` times the CPU oracle on the host cores on a bounded
+sample of the same workload per step (the paper has no code to run).
+Under torchrun (N > 1) every rank evaluates the whole workload on its own GPU
+(independent replicas; weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+from gen.bgp import GraphIndex, generate_bgps  # noqa: E402
+
+METRIC = "output bindings/s"
+UNIT = "bindings/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="university_bgp",
+                    choices=["university_bgp", "skewed_join", "pairwise_uniform"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- workloads
+
+class Workload:
+    name = ""
+    config = {}
+
+    def setup_gpu(self, ctx):
+        pass
+
+    def run_gpu(self, ctx):
+        """One step through the device-resident path; returns output rows."""
+        raise NotImplementedError
+
+    def run_e2e(self, ctx):
+        """One step through the C ABI with host buffers; returns (rows, h2d, d2h)."""
+        raise NotImplementedError
+
+    def run_oracle(self, sample_index):
+        """The oracle on a bounded sample; returns (rows, description)."""
+        raise NotImplementedError
+
+
+class UniversityBGP(Workload):
+    name = "university_bgp"
+
+    def __init__(self, n_triples=10_000_000, n_bgps=32, seed=2):
+        self.s, self.p, self.o = gen.university_graph(n_triples, seed=seed)
+        self.bgps = [b["patterns"] for b in generate_bgps(GraphIndex(self.s, self.p, self.o), n_bgps, seed=seed)]
+        self.config = {"workload": "university_bgp", "triples": n_triples, "predicates": 18, "bgps": n_bgps,
+                       "patterns_per_bgp": "3-6", "graph_seed": seed, "bgp_seed": seed,
+                       "l2": "flushed between steps (256 MiB write)"}
+        self._graph_set = None
+
+    def setup_gpu(self, ctx):
+        ctx.load_triples(self.s, self.p, self.o)
+
+    def run_gpu(self, ctx):
+        rows = 0
+        for b in self.bgps:
+            t = ctx.query(b)
+            rows += t.nrows
+            t.free()
+        return rows
+
+    def run_e2e(self, ctx):
+        rows = h2d = d2h = 0
+        for b in self.bgps:
+            t = ctx.query(b)
+            h2d += 16 * len(b)
+            vars_, cols = t.to_host()
+            d2h += sum(c.nbytes for c in cols)
+            rows += t.nrows
+            t.free()
+        return rows, h2d, d2h
+
+    def run_oracle(self, sample_index, budget_s=2.0):
+        import oracle
+        if self._graph_set is None:
+            self._graph_set = oracle.distinct_triples(self.s, self.p, self.o)
+        rows, done, t0 = 0, 0, time.perf_counter()
+        k = sample_index
+        while time.perf_counter() - t0 < budget_s and done < len(self.bgps):
+            b = self.bgps[k % len(self.bgps)]
+            rows += oracle.evaluate_bgp(self._graph_set, b, is_set=True)[1].shape[0]
+            k += 1
+            done += 1
+        return rows, done
+
+
+class SkewedJoin(Workload):
+    name = "skewed_join"
+
+    def __init__(self, log_a=26, log_b=24, log_keys=22):
+        self.A, self.B = gen.skewed_two_key(seed=3, log_a=log_a, log_b=log_b, log_keys=log_keys)
+        self.config = {"workload": "skewed_join", "rows_a": 1 << log_a, "rows_b": 1 << log_b,
+                       "key": "two shared variables packed in 64 bits", "zipf_s": 1.1, "key_ids": 1 << log_keys,
+                       "l2": "inputs larger than L2, flushed between steps"}
+
+    def setup_gpu(self, ctx):
+        import torch
+        self.tA = ctx.table(self.A.vars, [torch.from_numpy(c).cuda() for c in self.A.cols])
+        self.tB = ctx.table(self.B.vars, [torch.from_numpy(c).cuda() for c in self.B.cols])
+
+    def run_gpu(self, ctx):
+        t = ctx.join(self.tA, self.tB)
+        n = t.nrows
+        t.free()
+        return n
+
+    def run_e2e(self, ctx):
+        tA = ctx.table(self.A.vars, self.A.cols)
+        tB = ctx.table(self.B.vars, self.B.cols)
+        t = ctx.join(tA, tB)
+        vars_, cols = t.to_host()
+        n = t.nrows
+        h2d = sum(c.nbytes for c in self.A.cols + self.B.cols)
+        d2h = sum(c.nbytes for c in cols)
+        for x in (t, tA, tB):
+            x.free()
+        return n, h2d, d2h
+
+    def run_oracle(self, sample_index, budget_s=2.0):
+        import oracle
+        n = 1 << 18
+        lo = (sample_index * n) % self.A.nrows
+        A = gen.Table(self.A.vars, [c[lo:lo + n] for c in self.A.cols])
+        return oracle.join_mapreduce(A, self.B)[1].shape[0], n
+
+
+class PairwiseUniform(Workload):
+    name = "pairwise_uniform"
+
+    def __init__(self):
+        self.L, self.R = gen.pairwise_uniform(seed=1)
+        self.config = {"workload": "pairwise_uniform", "rows_left": 16384, "rows_right": 8192, "key_ids": 4096,
+                       "l2": "flushed between steps"}
+
+    def setup_gpu(self, ctx):
+        import torch
+        self.tL = ctx.table(self.L.vars, [torch.from_numpy(c).cuda() for c in self.L.cols])
+        self.tR = ctx.table(self.R.vars, [torch.from_numpy(c).cuda() for c in self.R.cols])
+
+    def run_gpu(self, ctx):
+        t = ctx.join(self.tL, self.tR)
+        n = t.nrows
+        t.free()
+        return n
+
+    def run_e2e(self, ctx):
+        tL = ctx.table(self.L.vars, self.L.cols)
+        tR = ctx.table(self.R.vars, self.R.cols)
+        t = ctx.join(tL, tR)
+        vars_, cols = t.to_host()
+        n = t.nrows
+        for x in (t, tL, tR):
+            x.free()
+        return n, sum(c.nbytes for c in self.L.cols + self.R.cols), sum(c.nbytes for c in cols)
+
+    def run_oracle(self, sample_index, budget_s=2.0):
+        import oracle
+        return oracle.join_mapreduce(self.L, self.R)[1].shape[0], 1
+
+
+WORKLOADS = {"university_bgp": UniversityBGP, "skewed_join": SkewedJoin, "pairwise_uniform": PairwiseUniform}
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of ``kernel`` from a committed ncu summary, if the
+    summary was taken from the current kernel sources (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    src = os.path.join(ROOT, "paper_1702_03484_gb300", "csrc", fields.get("source", "join.cu"))
+    if not os.path.exists(src):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("source_sha256") != digest:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]()
+    for i in range(args.warmup):
+        w.run_oracle(i, budget_s=0.5)
+    rows, units, t0 = 0, 0, time.perf_counter()
+    for i in range(args.steps):
+        r, u = w.run_oracle(args.warmup + i)
+        rows += r
+        units += u
+    dt = time.perf_counter() - t0
+    value = rows / dt
+    sample = (f"per step a ~2 s bounded sample of the {w.name} workload ({units} units in {args.steps} steps;"
+              f" units are BGPs or join slices), oracle in numpy on 1 core")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": w.config,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1702_03484_gb300 import Context
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with Context(device=local) as ctx:
+        w.setup_gpu(ctx)
+        stream = torch.cuda.current_stream(dev)
+        for _ in range(args.warmup):
+            w.run_gpu(ctx)
+        torch.cuda.synchronize()
+        ctx.reset_stats()
+        ctx.set_profiling(True)
+        launches0 = ctx.launch_count()
+        barrier()
+        torch.cuda.synchronize()
+        total_ms, rows = 0.0, 0
+        with ClockSampler(local) as clocks:
+            for _ in range(args.steps):
+                flush.fill_(1)  # evict the L2 between timed steps (not timed)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                rows += w.run_gpu(ctx)
+                b.record(stream)
+                b.synchronize()
+                total_ms += a.elapsed_time(b)
+        torch.cuda.synchronize()
+        barrier()
+        launches = ctx.launch_count() - launches0
+        stats = ctx.kernel_stats()
+        ctx.set_profiling(False)
+
+        # end to end through the C ABI with host buffers
+        for _ in range(2):
+            w.run_e2e(ctx)
+        torch.cuda.synchronize()
+        e_rows, h2d, d2h = 0, 0, 0
+        t0 = time.perf_counter()
+        e_steps = max(1, min(args.steps, 5))
+        for _ in range(e_steps):
+            r, hi, ho = w.run_e2e(ctx)
+            e_rows += r
+            h2d += hi
+            d2h += ho
+        torch.cuda.synchronize()
+        e_dt = time.perf_counter() - t0
+
+    t_max = total_ms
+    rows_all = rows
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        r = torch.tensor([rows], device=dev, dtype=torch.float64)
+        dist.all_reduce(r)
+        rows_all = float(r.item())
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    value = rows_all / (t_max / 1000.0)
+    peak, peak_kind = measured_peaks()
+    dom = max(stats.items(), key=lambda kv: kv[1]["device_ms"]) if stats else None
+    roofline = None
+    if dom:
+        name, st = dom
+        per_launch_s = st["device_ms"] / 1000.0 / st["launches"]
+        achieved = st["alg_bytes"] / st["launches"] / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic(name, w.name), "launches": st["launches"],
+                    "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
+                    "share_of_device_time": st["device_ms"] / sum(v["device_ms"] for v in stats.values())}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": w.config,
+            "rows_per_step": rows / args.steps,
+            "e2e": {"value": e_rows / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d // e_steps,
+                    "d2h_bytes_per_step": d2h // e_steps},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(),
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["device_ms"], 4)} for k, v in stats.items()}}
+    if not args.no_cpu_baseline and world == 1:
+        t0 = time.perf_counter()
+        crow, cunits = 0, 0
+        k = 0
+        while time.perf_counter() - t0 < 15.0:
+            r, u = w.run_oracle(k, budget_s=15.0 - (time.perf_counter() - t0))
+            crow += r
+            cunits += u
+            k += u
+        cdt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": crow / cdt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{cunits} units of the {w.name} workload (BGPs or join slices) in "
+                                          f"{cdt:.1f} s, numpy oracle, single thread"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

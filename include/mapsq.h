@@ -1,0 +1,222 @@
+/*
+ * mapsq.h - C ABI of a GB300-native implementation of MapSQ's MapReduce-based
+ * join of SPARQL triple-pattern partial matches (Feng, Zhang, Feng,
+ * "MapSQ: A MapReduce-based Framework for SPARQL Queries on GPU",
+ * arXiv 1702.03484).
+ *
+ * Model.  A graph is a set of dictionary-encoded triples (s, p, o), every term
+ * a uint32 id (0 .. 0xFFFFFFFF are all valid).  A triple pattern binds some of
+ * s, p, o to constants and the others to variables (ids 0..15).  Matching a
+ * pattern gives its partial-match table (Section 1, Table 1(a), 1(b)); two
+ * tables are joined on their shared variables (Algorithm 1); a basic graph
+ * pattern (BGP) is evaluated one pattern at a time, joining after each match
+ * (Section 2).  The host plans subqueries and join order; the device matches
+ * and joins (the paper's CPU/GPU coprocessing split, Section 2).
+ *
+ * Tables.  A table is structure-of-arrays: ``ncols`` uint32 columns of
+ * ``nrows`` rows; column c holds variable ``var[c]``.  Tables returned by the
+ * library are owned by the library until ``mapsq_table_free``; their columns
+ * are device pointers, 256-byte aligned.  A caller may also describe its own
+ * device columns in a ``mapsq_table`` it fills itself and pass it as an input;
+ * such columns must be 16-byte aligned and the caller keeps ownership (never
+ * pass such a table to ``mapsq_table_free``).
+ *
+ * Results are multisets of rows (bag semantics, no DISTINCT); row order is
+ * unspecified.
+ *
+ * Conventions.  Every int-returning call returns MAPSQ_OK (0) or a negative
+ * MAPSQ_ERR_* code; after an error, output arguments are left untouched and
+ * ``mapsq_last_error`` describes it.  Input pointers are borrowed for the call
+ * only.  All device work of a context is ordered on its CUDA stream; calls on
+ * one context must not run concurrently from several threads.  Calls that
+ * return a row count synchronise with that stream.
+ */
+#ifndef MAPSQ_H
+#define MAPSQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MAPSQ_MAX_VARS 16
+
+#if defined(__GNUC__)
+#define MAPSQ_API __attribute__((visibility("default")))
+#else
+#define MAPSQ_API
+#endif
+
+/* Status codes. */
+#define MAPSQ_OK 0
+#define MAPSQ_ERR_INVALID (-1)     /* bad argument (NULL, bad var id, bad size) */
+#define MAPSQ_ERR_UNSUPPORTED (-2) /* valid SPARQL outside the path: variable predicate, >2 join keys */
+#define MAPSQ_ERR_OOM (-3)         /* the allocator returned NULL */
+#define MAPSQ_ERR_BUDGET (-4)      /* the step needs more than the context's memory budget */
+#define MAPSQ_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define MAPSQ_ERR_TIMEOUT (-6)     /* a bounded device wait gave up (device status word) */
+#define MAPSQ_ERR_BUSY (-7)        /* the serving loop is not accepting work */
+#define MAPSQ_ERR_NOT_FOUND (-8)   /* unknown ticket */
+
+/* var_mask bits of a pattern: the field holds a variable id instead of a term. */
+#define MAPSQ_VAR_S 1u
+#define MAPSQ_VAR_P 2u
+#define MAPSQ_VAR_O 4u
+
+/* Join algorithms for mapsq_join_opts.algorithm. */
+#define MAPSQ_JOIN_AUTO 0
+#define MAPSQ_JOIN_HASH 1
+
+typedef struct mapsq_ctx mapsq_ctx;
+
+/* Device memory provider.  ``alloc`` returns device memory of at least
+ * ``bytes`` bytes usable on ``stream`` (a cudaStream_t) or NULL; ``free``
+ * releases a block obtained from ``alloc``.  NULL allocator: the library uses
+ * its own stream-ordered pool (cudaMallocAsync). */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user, void* stream);
+  void (*free)(void* ptr, size_t bytes, void* user, void* stream);
+  void* user;
+} mapsq_allocator;
+
+/* One triple pattern (Section 1).  A field whose MAPSQ_VAR_* bit is set in
+ * ``var_mask`` holds a variable id (0..15), otherwise a term id.  The predicate
+ * must be a constant (a variable predicate gives MAPSQ_ERR_UNSUPPORTED). */
+typedef struct {
+  uint32_t s, p, o, var_mask;
+} mapsq_pattern;
+
+/* A binding table (structure of arrays), see "Tables" above.  A table with
+ * ncols == 0 is a set of empty bindings: nrows is 0 (no solution) or 1 (the
+ * pattern held, no variable bound). */
+typedef struct {
+  uint64_t nrows;
+  uint32_t ncols;
+  int32_t var[MAPSQ_MAX_VARS];
+  uint32_t* col[MAPSQ_MAX_VARS];
+  int32_t on_device;
+} mapsq_table;
+
+/* Join options; a NULL pointer or zero fields choose defaults. */
+typedef struct {
+  int32_t algorithm;     /* MAPSQ_JOIN_AUTO or MAPSQ_JOIN_HASH */
+  int32_t block_threads; /* threads per CTA of the write pass (multiple of 32, <= 1024) */
+  int32_t tile_rows;     /* output rows per CTA tile of the write pass (multiple of 4 * block_threads) */
+  int32_t reserved;
+} mapsq_join_opts;
+
+/* Per-kernel device time, collected while profiling is on (mapsq_set_profiling).
+ * ``alg_bytes`` sums each launch's algorithmic bytes: the bytes the step must
+ * read and write at minimum (inputs once, outputs once). */
+typedef struct {
+  char name[48];
+  uint64_t launches;
+  double device_ms;
+  double alg_bytes;
+} mapsq_kernel_stat;
+
+/* Create a context on CUDA device ``device``.  ``cuda_stream`` (a cudaStream_t)
+ * orders all device work; NULL creates a private non-blocking stream (pass
+ * cudaStreamLegacy, (void*)1, for the legacy default stream).
+ * ``mem_budget_bytes`` bounds the device memory of intermediate and result
+ * tables plus scratch (0 = unbounded).  Errors: INVALID (out == NULL, bad
+ * device), CUDA. */
+MAPSQ_API int mapsq_create(mapsq_ctx** out, int device, const mapsq_allocator* allocator, void* cuda_stream,
+                 uint64_t mem_budget_bytes);
+
+/* Synchronise, free the triple store and every table still owned by ``ctx``, and
+ * the context itself.  NULL is a no-op returning MAPSQ_OK. */
+MAPSQ_API int mapsq_destroy(mapsq_ctx* ctx);
+
+/* Replace the stream that orders the context's work (a cudaStream_t; NULL =
+ * the private stream).  Earlier work is not waited for. */
+MAPSQ_API int mapsq_set_stream(mapsq_ctx* ctx, void* cuda_stream);
+
+/* Description of the last error on this context (never NULL). */
+MAPSQ_API const char* mapsq_last_error(const mapsq_ctx* ctx);
+
+/* Name of a status code. */
+MAPSQ_API const char* mapsq_strerror(int status);
+
+/* Load a graph: ``n`` triples given as three uint32 columns (host pointers, or
+ * device pointers when ``ptrs_on_device`` is nonzero).  The graph is a set
+ * (RDF): duplicate triples are dropped.  Builds the device-resident store: per
+ * predicate, the (s, o) pairs sorted by s then o, and the (o, s) pairs sorted by
+ * o then s (the index that replaces the paper's partial-matching engine,
+ * Section 2).  Replaces any previous store; tables from earlier scans stay
+ * valid.  Synchronises.  Errors: INVALID, OOM, BUDGET, CUDA. */
+MAPSQ_API int mapsq_load_triples(mapsq_ctx* ctx, const uint32_t* s, const uint32_t* p, const uint32_t* o, uint64_t n,
+                       int ptrs_on_device);
+
+/* Number of distinct triples and predicates of the loaded store. */
+MAPSQ_API int mapsq_store_info(mapsq_ctx* ctx, uint64_t* n_triples, uint32_t* n_predicates);
+
+/* Partial matches of one triple pattern (Section 1, Table 1(a) and 1(b);
+ * Section 2, first step of query answering).  The result has one column per
+ * distinct variable, in the order s, o; a variable in both places keeps the
+ * triples with s == o.  Both constants: a 0-column table of 0 or 1 rows.
+ * Synchronises.  Errors: INVALID (NULL, var id > 15), UNSUPPORTED (variable
+ * predicate), OOM, BUDGET, CUDA; INVALID if no store is loaded. */
+MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_table** out);
+
+/* Join two tables on their shared variables (Algorithm 1, the MapReduce-based
+ * join: map each row to (key = shared variables, value = other columns, label
+ * LEFT/RIGHT), shuffle by key, and reduce each key to every LEFT x RIGHT pair).
+ * Output columns: the shared variables in ascending id, then the left table's
+ * other columns in order, then the right table's (Table 1(c)).  No shared
+ * variable: the cross product.  Input columns must be on the device.
+ * Synchronises once (to size the output).  Errors: INVALID, UNSUPPORTED (more
+ * than two shared variables), OOM, BUDGET, CUDA. */
+MAPSQ_API int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right, mapsq_table** out,
+               const mapsq_join_opts* opts);
+
+/* Evaluate a BGP of ``n`` patterns (Section 2: match each pattern, join the
+ * partial results after each match).  The host orders the patterns: the one
+ * with fewest matches first, then repeatedly the one with fewest matches among
+ * those sharing a variable with the joined ones.  Result columns are the BGP's
+ * variables in ascending id.  Errors: as mapsq_scan_pattern and mapsq_join. */
+MAPSQ_API int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out);
+
+/* Copy ``ncols`` columns of ``nrows`` rows (host pointers, or device pointers if
+ * ``on_device``) into a new library-owned device table with variables ``var``.
+ * ncols == 0 makes a 0-column table of ``nrows`` (0 or 1) empty bindings.
+ * Errors: INVALID (ncols > 16, duplicate or out-of-range var ids, NULL), OOM,
+ * BUDGET, CUDA. */
+MAPSQ_API int mapsq_table_from_columns(mapsq_ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var,
+                             const uint32_t* const* cols, int on_device, mapsq_table** out);
+
+/* Copy every column of ``t`` to caller-owned host buffers (host_cols[c] holds
+ * t->nrows uint32).  Synchronises.  Errors: INVALID, CUDA. */
+MAPSQ_API int mapsq_table_to_host(mapsq_ctx* ctx, const mapsq_table* t, uint32_t* const* host_cols);
+
+/* Release a table returned by the library (NULL is a no-op). */
+MAPSQ_API void mapsq_table_free(mapsq_ctx* ctx, mapsq_table* t);
+
+/* Wait for the context's stream and check the device status word.  Errors:
+ * CUDA, TIMEOUT. */
+MAPSQ_API int mapsq_sync(mapsq_ctx* ctx);
+
+/* Device memory currently held for tables and scratch, and its high-water mark. */
+MAPSQ_API int mapsq_memory_in_use(mapsq_ctx* ctx, uint64_t* bytes, uint64_t* peak_bytes);
+
+/* Turn per-kernel timing on (1) or off (0).  While on, every launch is bracketed
+ * by CUDA events on the context's stream. */
+MAPSQ_API int mapsq_set_profiling(mapsq_ctx* ctx, int enable);
+
+/* Per-kernel totals since profiling was last turned on or reset: writes up to
+ * ``cap`` entries and their number to ``*n``.  Synchronises. */
+MAPSQ_API int mapsq_kernel_stats(mapsq_ctx* ctx, mapsq_kernel_stat* out, uint32_t cap, uint32_t* n);
+
+/* Clear the per-kernel totals. */
+MAPSQ_API int mapsq_reset_stats(mapsq_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched since it was created. */
+MAPSQ_API int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAPSQ_H */

@@ -1,0 +1,491 @@
+// C ABI entry points: contexts, memory, tables, profiling, and the BGP planner
+// (the host side of the paper's CPU/GPU coprocessing split, Section 2).
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace mapsq {
+
+const char* const kKernelNames[K_COUNT_KERNELS] = {
+    "store_radix_histogram", "store_radix_scatter", "store_dedup", "store_predicate_heads",
+    "scan_ranges",           "scan_emit",           "scan_filter", "prefix_sum",
+    "hash_insert",           "hash_scatter",        "probe_count", "join_write",
+    "cross_write",           "copy"};
+
+int set_error(Ctx* ctx, int code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(Ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
+  return set_error(ctx, MAPSQ_ERR_CUDA, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+int dev_alloc(Ctx* ctx, size_t bytes, void** out) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+    return set_error(ctx, MAPSQ_ERR_BUDGET, "allocation of %zu bytes exceeds the budget (%llu in use of %llu)",
+                     bytes, (unsigned long long)ctx->in_use, (unsigned long long)ctx->budget);
+  void* p = nullptr;
+  if (ctx->has_allocator) {
+    p = ctx->allocator.alloc(bytes, ctx->allocator.user, ctx->stream);
+  } else {
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, ctx->pool, ctx->stream);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      p = nullptr;
+    } else if (e != cudaSuccess) {
+      return cuda_fail(ctx, e, "cudaMallocFromPoolAsync", __FILE__, __LINE__);
+    }
+  }
+  if (!p) return set_error(ctx, MAPSQ_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+  ctx->in_use += bytes;
+  ctx->peak = std::max(ctx->peak, ctx->in_use);
+  *out = p;
+  return MAPSQ_OK;
+}
+
+void dev_free(Ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (ctx->has_allocator)
+    ctx->allocator.free(p, bytes, ctx->allocator.user, ctx->stream);
+  else
+    cudaFreeAsync(p, ctx->stream);
+  ctx->in_use -= std::min<uint64_t>(ctx->in_use, bytes);
+}
+
+int table_alloc(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, TableImpl** out) {
+  if (ncols > MAPSQ_MAX_VARS) return set_error(ctx, MAPSQ_ERR_INVALID, "table with %u columns", ncols);
+  TableImpl* t = new (std::nothrow) TableImpl();
+  if (!t) return set_error(ctx, MAPSQ_ERR_OOM, "host allocation failed");
+  t->magic = kTableMagic;
+  t->pub.nrows = nrows;
+  t->pub.ncols = ncols;
+  t->pub.on_device = 1;
+  for (uint32_t c = 0; c < MAPSQ_MAX_VARS; ++c) {
+    t->pub.var[c] = c < ncols ? var[c] : -1;
+    t->pub.col[c] = nullptr;
+  }
+  // stride rounded to 64 rows: every column starts 256-byte aligned
+  uint64_t stride = (nrows + 63) & ~uint64_t(63);
+  size_t bytes = size_t(stride) * ncols * sizeof(uint32_t);
+  if (bytes) {
+    int rc = dev_alloc(ctx, bytes, &t->block);
+    if (rc != MAPSQ_OK) {
+      delete t;
+      return rc;
+    }
+    t->bytes = bytes;
+    for (uint32_t c = 0; c < ncols; ++c) t->pub.col[c] = static_cast<uint32_t*>(t->block) + stride * c;
+  }
+  ctx->live_tables.push_back(t);
+  *out = t;
+  return MAPSQ_OK;
+}
+
+void table_release(Ctx* ctx, TableImpl* t) {
+  if (!t) return;
+  auto it = std::find(ctx->live_tables.begin(), ctx->live_tables.end(), t);
+  if (it == ctx->live_tables.end()) return;  // not ours, or already released
+  ctx->live_tables.erase(it);
+  dev_free(ctx, t->block, t->bytes);
+  t->magic = 0;
+  delete t;
+}
+
+int prof_begin(Ctx* ctx, int kid) {
+  if (!ctx->profiling) return -1;
+  LaunchRecord r{kid, nullptr, nullptr, 0.0};
+  for (cudaEvent_t* e : {&r.start, &r.stop}) {
+    if (!ctx->free_events.empty()) {
+      *e = ctx->free_events.back();
+      ctx->free_events.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      return -1;
+    }
+  }
+  cudaEventRecord(r.start, ctx->stream);
+  ctx->pending.push_back(r);
+  return int(ctx->pending.size()) - 1;
+}
+
+void prof_end(Ctx* ctx, int rec, double alg_bytes) {
+  if (rec < 0 || !ctx->profiling || rec >= int(ctx->pending.size())) return;
+  cudaEventRecord(ctx->pending[rec].stop, ctx->stream);
+  ctx->pending[rec].bytes = alg_bytes;
+}
+
+static int drain_profile(Ctx* ctx) {
+  if (ctx->pending.empty()) return MAPSQ_OK;
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (auto& r : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      ctx->totals[r.kid].launches += 1;
+      ctx->totals[r.kid].ms += ms;
+      ctx->totals[r.kid].bytes += r.bytes;
+    }
+    ctx->free_events.push_back(r.start);
+    ctx->free_events.push_back(r.stop);
+  }
+  ctx->pending.clear();
+  return MAPSQ_OK;
+}
+
+int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count) {
+  if (count < 1 || count > 32) return set_error(ctx, MAPSQ_ERR_INVALID, "read_u64 of %d words", count);
+  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned, dptr, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost, ctx->stream));
+  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  memcpy(host, ctx->h_pinned, sizeof(uint64_t) * count);
+  return check_status(ctx);
+}
+
+int check_status(Ctx* ctx) {
+  // h_pinned[32] holds the status word read by the last synchronising call
+  uint32_t st = uint32_t(ctx->h_pinned[32] & 0xFFFFFFFFu);
+  if (st == 0) return MAPSQ_OK;
+  ctx->h_pinned[32] = 0;
+  MQ_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream));
+  if (st & 2u) return set_error(ctx, MAPSQ_ERR_TIMEOUT, "a bounded device wait gave up (status 0x%x)", st);
+  return set_error(ctx, MAPSQ_ERR_CUDA, "device status 0x%x (hash table full or index out of range)", st);
+}
+
+static bool pattern_var(const mapsq_pattern& tp, uint32_t bit, uint32_t* v) {
+  if (!(tp.var_mask & bit)) return false;
+  *v = bit == MAPSQ_VAR_S ? tp.s : bit == MAPSQ_VAR_P ? tp.p : tp.o;
+  return true;
+}
+
+static uint32_t pattern_var_set(const mapsq_pattern& tp) {
+  uint32_t m = 0, v;
+  if (pattern_var(tp, MAPSQ_VAR_S, &v)) m |= 1u << v;
+  if (pattern_var(tp, MAPSQ_VAR_O, &v)) m |= 1u << v;
+  return m;
+}
+
+// Permute the columns of a result so that its variables are in ascending id
+// (a pointer permutation: no data moves).
+static void canonical_columns(mapsq_table* t) {
+  uint32_t n = t->ncols;
+  for (uint32_t i = 1; i < n; ++i)
+    for (uint32_t j = i; j > 0 && t->var[j - 1] > t->var[j]; --j) {
+      std::swap(t->var[j - 1], t->var[j]);
+      std::swap(t->col[j - 1], t->col[j]);
+    }
+}
+
+}  // namespace mapsq
+
+using namespace mapsq;
+
+extern "C" {
+
+const char* mapsq_strerror(int status) {
+  switch (status) {
+    case MAPSQ_OK: return "ok";
+    case MAPSQ_ERR_INVALID: return "invalid argument";
+    case MAPSQ_ERR_UNSUPPORTED: return "unsupported";
+    case MAPSQ_ERR_OOM: return "out of device memory";
+    case MAPSQ_ERR_BUDGET: return "memory budget exceeded";
+    case MAPSQ_ERR_CUDA: return "CUDA error";
+    case MAPSQ_ERR_TIMEOUT: return "device wait timed out";
+    case MAPSQ_ERR_BUSY: return "busy";
+    case MAPSQ_ERR_NOT_FOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+const char* mapsq_last_error(const mapsq_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int mapsq_create(mapsq_ctx** out, int device, const mapsq_allocator* allocator, void* cuda_stream,
+                 uint64_t mem_budget_bytes) {
+  if (!out) return MAPSQ_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MAPSQ_ERR_INVALID;
+  }
+  if (allocator && (!allocator->alloc || !allocator->free)) return MAPSQ_ERR_INVALID;
+  Ctx* ctx = new (std::nothrow) Ctx();
+  if (!ctx) return MAPSQ_ERR_OOM;
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes;
+  int rc = MAPSQ_OK;
+  auto fail = [&](int code) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+    return code;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
+  ctx->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->own_stream;
+  if (allocator) {
+    ctx->has_allocator = true;
+    ctx->allocator = *allocator;
+  } else {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
+    uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (cudaMallocHost(&ctx->h_pinned, 64 * sizeof(uint64_t)) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
+  memset(ctx->h_pinned, 0, 64 * sizeof(uint64_t));
+  void* st = nullptr;
+  rc = dev_alloc(ctx, 256, &st);
+  if (rc != MAPSQ_OK) return fail(rc);
+  ctx->d_status = static_cast<uint32_t*>(st);
+  if (cudaMemsetAsync(ctx->d_status, 0, 256, ctx->stream) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
+  *out = ctx;
+  return MAPSQ_OK;
+}
+
+int mapsq_destroy(mapsq_ctx* ctx) {
+  if (!ctx) return MAPSQ_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& r : ctx->pending) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : ctx->free_events) cudaEventDestroy(e);
+  while (!ctx->live_tables.empty()) table_release(ctx, ctx->live_tables.back());
+  store_release(ctx);
+  dev_free(ctx, ctx->d_status, 256);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+  return MAPSQ_OK;
+}
+
+int mapsq_set_stream(mapsq_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  ctx->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->own_stream;
+  return MAPSQ_OK;
+}
+
+int mapsq_load_triples(mapsq_ctx* ctx, const uint32_t* s, const uint32_t* p, const uint32_t* o, uint64_t n,
+                       int ptrs_on_device) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  if (n && (!s || !p || !o)) return set_error(ctx, MAPSQ_ERR_INVALID, "NULL triple column");
+  if (n >= (uint64_t(1) << 32)) return set_error(ctx, MAPSQ_ERR_INVALID, "at most 2^32-1 triples");
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  return store_build(ctx, s, p, o, n, ptrs_on_device);
+}
+
+int mapsq_store_info(mapsq_ctx* ctx, uint64_t* n_triples, uint32_t* n_predicates) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  if (n_triples) *n_triples = ctx->store.n;
+  if (n_predicates) *n_predicates = uint32_t(ctx->store.pred_id.size());
+  return MAPSQ_OK;
+}
+
+int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_table** out) {
+  if (!ctx || !tp || !out) return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  MQ_TRY(validate_pattern(ctx, *tp));
+  if (!ctx->store.loaded) return set_error(ctx, MAPSQ_ERR_INVALID, "no triple store loaded");
+  PatternRange r;
+  MQ_TRY(scan_ranges(ctx, tp, 1, &r));
+  TableImpl* t = nullptr;
+  MQ_TRY(scan_emit(ctx, *tp, r, &t));
+  *out = &t->pub;
+  return MAPSQ_OK;
+}
+
+int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right, mapsq_table** out,
+               const mapsq_join_opts* opts) {
+  if (!ctx || !left || !right || !out)
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  TableImpl* t = nullptr;
+  MQ_TRY(join_tables(ctx, left, right, opts, &t));
+  *out = &t->pub;
+  return MAPSQ_OK;
+}
+
+int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out) {
+  if (!ctx || !bgp || !out || n == 0)
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument or empty BGP") : MAPSQ_ERR_INVALID;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  for (uint32_t i = 0; i < n; ++i) MQ_TRY(validate_pattern(ctx, bgp[i]));
+  if (!ctx->store.loaded) return set_error(ctx, MAPSQ_ERR_INVALID, "no triple store loaded");
+  std::vector<PatternRange> ranges(n);
+  MQ_TRY(scan_ranges(ctx, bgp, n, ranges.data()));
+
+  // Greedy order: fewest matches first, then the connected pattern with fewest matches.
+  std::vector<uint32_t> rest(n), order;
+  for (uint32_t i = 0; i < n; ++i) rest[i] = i;
+  auto size_of = [&](uint32_t i) { return ranges[i].hi - ranges[i].lo; };
+  std::stable_sort(rest.begin(), rest.end(), [&](uint32_t a, uint32_t b) { return size_of(a) < size_of(b); });
+  order.push_back(rest.front());
+  rest.erase(rest.begin());
+  uint32_t seen = pattern_var_set(bgp[order[0]]);
+  while (!rest.empty()) {
+    auto it = std::find_if(rest.begin(), rest.end(), [&](uint32_t i) { return (pattern_var_set(bgp[i]) & seen) != 0; });
+    if (it == rest.end()) it = rest.begin();
+    order.push_back(*it);
+    seen |= pattern_var_set(bgp[*it]);
+    rest.erase(it);
+  }
+
+  TableImpl* acc = nullptr;
+  int rc = scan_emit(ctx, bgp[order[0]], ranges[order[0]], &acc);
+  if (rc != MAPSQ_OK) return rc;
+  for (size_t k = 1; k < order.size(); ++k) {
+    TableImpl* part = nullptr;
+    rc = scan_emit(ctx, bgp[order[k]], ranges[order[k]], &part);
+    if (rc != MAPSQ_OK) {
+      table_release(ctx, acc);
+      return rc;
+    }
+    TableImpl* joined = nullptr;
+    rc = join_tables(ctx, &acc->pub, &part->pub, nullptr, &joined);
+    table_release(ctx, part);
+    table_release(ctx, acc);
+    if (rc != MAPSQ_OK) return rc;
+    acc = joined;
+  }
+  canonical_columns(&acc->pub);
+  *out = &acc->pub;
+  return MAPSQ_OK;
+}
+
+int mapsq_table_from_columns(mapsq_ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var,
+                             const uint32_t* const* cols, int on_device, mapsq_table** out) {
+  if (!ctx || !out || (ncols && (!var || !cols)))
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (ncols > MAPSQ_MAX_VARS) return set_error(ctx, MAPSQ_ERR_INVALID, "more than 16 columns");
+  if (ncols == 0 && nrows > 1) return set_error(ctx, MAPSQ_ERR_INVALID, "a 0-column table has 0 or 1 rows");
+  uint32_t seen = 0;
+  for (uint32_t c = 0; c < ncols; ++c) {
+    if (var[c] < 0 || var[c] >= MAPSQ_MAX_VARS) return set_error(ctx, MAPSQ_ERR_INVALID, "variable id %d", var[c]);
+    if (seen & (1u << var[c])) return set_error(ctx, MAPSQ_ERR_INVALID, "variable %d twice", var[c]);
+    seen |= 1u << var[c];
+    if (nrows && !cols[c]) return set_error(ctx, MAPSQ_ERR_INVALID, "NULL column %u", c);
+  }
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  TableImpl* t = nullptr;
+  MQ_TRY(table_alloc(ctx, nrows, ncols, var, &t));
+  for (uint32_t c = 0; c < ncols && nrows; ++c) {
+    cudaError_t e;
+    if (on_device) {
+      int rc = copy_u32(ctx, t->pub.col[c], cols[c], nrows);
+      if (rc != MAPSQ_OK) {
+        table_release(ctx, t);
+        return rc;
+      }
+      continue;
+    }
+    e = cudaMemcpyAsync(t->pub.col[c], cols[c], nrows * sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+      table_release(ctx, t);
+      return cuda_fail(ctx, e, "cudaMemcpyAsync", __FILE__, __LINE__);
+    }
+  }
+  // host sources are borrowed for the call only
+  if (!on_device) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      table_release(ctx, t);
+      return cuda_fail(ctx, e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    }
+  }
+  *out = &t->pub;
+  return MAPSQ_OK;
+}
+
+int mapsq_table_to_host(mapsq_ctx* ctx, const mapsq_table* t, uint32_t* const* host_cols) {
+  if (!ctx || !t || (t->ncols && !host_cols))
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  for (uint32_t c = 0; c < t->ncols && t->nrows; ++c) {
+    if (!host_cols[c]) return set_error(ctx, MAPSQ_ERR_INVALID, "NULL host column %u", c);
+    MQ_CUDA(cudaMemcpyAsync(host_cols[c], t->col[c], t->nrows * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  }
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MAPSQ_OK;
+}
+
+void mapsq_table_free(mapsq_ctx* ctx, mapsq_table* t) {
+  if (!ctx || !t) return;
+  TableImpl* impl = reinterpret_cast<TableImpl*>(t);
+  table_release(ctx, impl);
+}
+
+int mapsq_sync(mapsq_ctx* ctx) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
+}
+
+int mapsq_memory_in_use(mapsq_ctx* ctx, uint64_t* bytes, uint64_t* peak_bytes) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  if (bytes) *bytes = ctx->in_use;
+  if (peak_bytes) *peak_bytes = ctx->peak;
+  return MAPSQ_OK;
+}
+
+int mapsq_set_profiling(mapsq_ctx* ctx, int enable) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  if (!enable) MQ_TRY(drain_profile(ctx));
+  ctx->profiling = enable != 0;
+  return MAPSQ_OK;
+}
+
+int mapsq_kernel_stats(mapsq_ctx* ctx, mapsq_kernel_stat* out, uint32_t cap, uint32_t* n) {
+  if (!ctx || !n || (cap && !out)) return MAPSQ_ERR_INVALID;
+  MQ_TRY(drain_profile(ctx));
+  uint32_t k = 0;
+  for (int i = 0; i < K_COUNT_KERNELS; ++i) {
+    if (!ctx->totals[i].launches) continue;
+    if (k < cap) {
+      memset(&out[k], 0, sizeof(mapsq_kernel_stat));
+      strncpy(out[k].name, kKernelNames[i], sizeof(out[k].name) - 1);
+      out[k].launches = ctx->totals[i].launches;
+      out[k].device_ms = ctx->totals[i].ms;
+      out[k].alg_bytes = ctx->totals[i].bytes;
+    }
+    ++k;
+  }
+  *n = k;
+  return MAPSQ_OK;
+}
+
+int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches) {
+  if (!ctx || !launches) return MAPSQ_ERR_INVALID;
+  *launches = ctx->launches;
+  return MAPSQ_OK;
+}
+
+int mapsq_reset_stats(mapsq_ctx* ctx) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  MQ_TRY(drain_profile(ctx));
+  for (auto& t : ctx->totals) t = KernelTotals{};
+  return MAPSQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// Internal declarations shared by the translation units of libmapsq.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "mapsq.h"
+
+namespace mapsq {
+
+// Kernels timed by the profiling switch (mapsq_set_profiling).
+enum KernelId {
+  K_STORE_HIST = 0,
+  K_STORE_SCATTER,
+  K_STORE_DEDUP,
+  K_PRED_HEADS,
+  K_SCAN_RANGES,
+  K_SCAN_EMIT,
+  K_SCAN_FILTER,
+  K_PREFIX_SUM,
+  K_HASH_INSERT,
+  K_HASH_SCATTER,
+  K_PROBE_COUNT,
+  K_JOIN_WRITE,
+  K_CROSS_WRITE,
+  K_COPY,
+  K_COUNT_KERNELS
+};
+
+extern const char* const kKernelNames[K_COUNT_KERNELS];
+
+// A library-owned table: the public struct first, so a mapsq_table* handed out
+// by the library converts back to its TableImpl.
+struct TableImpl {
+  mapsq_table pub;
+  void* block;   // one allocation holding every column
+  size_t bytes;
+  uint32_t magic;
+};
+constexpr uint32_t kTableMagic = 0x7AB1E5u;
+
+// Device-resident triple store: per predicate, SO- and OS-sorted column pairs.
+struct Store {
+  bool loaded = false;
+  uint64_t n = 0;                   // distinct triples
+  std::vector<uint32_t> pred_id;    // sorted distinct predicate ids (host mirror)
+  std::vector<uint64_t> pred_begin; // segment [pred_begin[k], pred_begin[k+1]) of predicate pred_id[k]
+  uint32_t* so_s = nullptr;         // sorted by (p, s, o)
+  uint32_t* so_o = nullptr;
+  uint32_t* os_o = nullptr;         // sorted by (p, o, s)
+  uint32_t* os_s = nullptr;
+  void* block = nullptr;
+  size_t bytes = 0;
+};
+
+struct LaunchRecord {
+  int kid;
+  cudaEvent_t start, stop;
+  double bytes;
+};
+
+struct KernelTotals {
+  uint64_t launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+};
+
+}  // namespace mapsq
+
+struct mapsq_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  bool has_allocator = false;
+  mapsq_allocator allocator{};
+  cudaMemPool_t pool = nullptr;
+  uint64_t budget = 0;
+  uint64_t in_use = 0;
+  uint64_t peak = 0;
+  std::string err;
+  mapsq::Store store;
+  uint32_t* d_status = nullptr;    // device status word: 0 = fine
+  uint64_t* h_pinned = nullptr;    // small pinned buffer for device->host reads
+  bool profiling = false;
+  uint64_t launches = 0;          // kernels launched by this context
+  std::vector<mapsq::LaunchRecord> pending;
+  std::vector<cudaEvent_t> free_events;
+  mapsq::KernelTotals totals[mapsq::K_COUNT_KERNELS];
+  std::vector<mapsq::TableImpl*> live_tables;
+};
+
+namespace mapsq {
+
+using Ctx = mapsq_ctx;
+
+int set_error(Ctx* ctx, int code, const char* fmt, ...);
+int cuda_fail(Ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+
+#define MQ_CUDA(call)                                                     \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) return ::mapsq::cuda_fail(ctx, e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define MQ_TRY(call)         \
+  do {                       \
+    int rc_ = (call);        \
+    if (rc_ != MAPSQ_OK) return rc_; \
+  } while (0)
+
+// Device memory through the context's allocator, counted against its budget.
+int dev_alloc(Ctx* ctx, size_t bytes, void** out);
+void dev_free(Ctx* ctx, void* p, size_t bytes);
+
+// RAII holder for scratch allocations inside one call.
+struct Scratch {
+  Ctx* ctx;
+  std::vector<std::pair<void*, size_t>> blocks;
+  explicit Scratch(Ctx* c) : ctx(c) {}
+  ~Scratch() {
+    for (auto& b : blocks) dev_free(ctx, b.first, b.second);
+  }
+  template <class T>
+  int get(size_t count, T** out) {
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    int rc = dev_alloc(ctx, bytes, &p);
+    if (rc != MAPSQ_OK) return rc;
+    blocks.push_back({p, bytes});
+    *out = static_cast<T*>(p);
+    return MAPSQ_OK;
+  }
+};
+
+// Allocate a library-owned table with room for nrows x ncols (columns 256-byte aligned).
+int table_alloc(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, TableImpl** out);
+void table_release(Ctx* ctx, TableImpl* t);
+
+// Profiling brackets around one launch (no-ops while profiling is off).
+int prof_begin(Ctx* ctx, int kid);
+void prof_end(Ctx* ctx, int rec, double alg_bytes);
+
+// Read a few 64-bit words back from the device (synchronises the stream).
+int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count);
+
+// Device status word check after a synchronisation.
+int check_status(Ctx* ctx);
+
+// Primitives (prim.cu).
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+int prefix_sum_u32_u64(Ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n);
+int prefix_sum_u32_u32(Ctx* ctx, const uint32_t* in, uint32_t* out, uint64_t n);
+int copy_u32(Ctx* ctx, uint32_t* dst, const uint32_t* src, uint64_t n);
+
+// Store (store.cu).
+int store_build(Ctx* ctx, const uint32_t* s, const uint32_t* p, const uint32_t* o, uint64_t n, int on_device);
+void store_release(Ctx* ctx);
+
+// Pattern scan (scan.cu).
+struct PatternRange {
+  uint64_t lo, hi;  // row range in the chosen order; hi - lo = matches (before the s==o filter)
+  int32_t order;    // 0: SO columns, 1: OS columns, -1: no match
+  int32_t kind;     // see scan.cu
+};
+int validate_pattern(Ctx* ctx, const mapsq_pattern& tp);
+int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* out);
+int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImpl** out);
+
+// Join (join.cu).
+int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
+                TableImpl** out);
+
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+}  // namespace mapsq

@@ -1,0 +1,228 @@
+// Pattern scan: the partial matches of one triple pattern (Section 1; the
+// partial-matching step of Section 2), read from the sorted store instead of a
+// CPU engine.
+//
+// With a constant predicate p the candidates are p's segment of the store.  A
+// constant subject selects a run of the (p, s, o) order, a constant object a
+// run of the (p, o, s) order; both runs are found by binary search on the
+// device and the remaining variable's column is copied out.  Two variables
+// copy the whole segment; one variable in both places keeps the rows with
+// s == o.  Two constants test membership and give 0 or 1 empty binding.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace mapsq {
+
+namespace {
+
+enum ScanKind : int32_t {
+  KIND_NONE = 0,    // predicate not in the store: no match
+  KIND_EXIST = 1,   // s and o constant
+  KIND_S_BOUND = 2, // s constant, o variable
+  KIND_O_BOUND = 3, // o constant, s variable
+  KIND_TWO_VARS = 4,
+  KIND_SAME_VAR = 5
+};
+
+struct RangeQuery {
+  uint64_t b, e;     // predicate segment
+  uint32_t v0, v1;   // constants
+  int32_t kind;
+  int32_t pad;
+};
+
+struct StoreCols {
+  const uint32_t* so_s;
+  const uint32_t* so_o;
+  const uint32_t* os_o;
+  const uint32_t* os_s;
+};
+
+__device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t* a, uint64_t lo, uint64_t hi, uint32_t v) {
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t upper_bound_u32(const uint32_t* a, uint64_t lo, uint64_t hi, uint32_t v) {
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (a[mid] <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void scan_ranges_kernel(const RangeQuery* __restrict__ q, uint32_t n, StoreCols st,
+                                   uint64_t* __restrict__ out) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  RangeQuery r = q[i];
+  uint64_t lo = 0, hi = 0;
+  switch (r.kind) {
+    case KIND_S_BOUND:
+      lo = lower_bound_u32(st.so_s, r.b, r.e, r.v0);
+      hi = upper_bound_u32(st.so_s, lo, r.e, r.v0);
+      break;
+    case KIND_O_BOUND:
+      lo = lower_bound_u32(st.os_o, r.b, r.e, r.v1);
+      hi = upper_bound_u32(st.os_o, lo, r.e, r.v1);
+      break;
+    case KIND_EXIST: {
+      uint64_t a = lower_bound_u32(st.so_s, r.b, r.e, r.v0);
+      uint64_t z = upper_bound_u32(st.so_s, a, r.e, r.v0);
+      uint64_t k = lower_bound_u32(st.so_o, a, z, r.v1);
+      lo = k;
+      hi = (k < z && st.so_o[k] == r.v1) ? k + 1 : k;
+      break;
+    }
+    case KIND_TWO_VARS:
+    case KIND_SAME_VAR:
+      lo = r.b;
+      hi = r.e;
+      break;
+    default:
+      break;
+  }
+  out[2 * i] = lo;
+  out[2 * i + 1] = hi;
+}
+
+__global__ void same_var_flags_kernel(const uint32_t* __restrict__ s, const uint32_t* __restrict__ o, uint64_t n,
+                                      uint32_t* __restrict__ flag) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    flag[i] = s[i] == o[i] ? 1u : 0u;
+}
+
+__global__ void same_var_compact_kernel(const uint32_t* __restrict__ s, uint64_t n, const uint32_t* __restrict__ flag,
+                                        const uint64_t* __restrict__ pos, uint32_t* __restrict__ out) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
+    if (flag[i]) out[pos[i]] = s[i];
+}
+
+int32_t pattern_kind(const mapsq_pattern& tp) {
+  bool sv = tp.var_mask & MAPSQ_VAR_S, ov = tp.var_mask & MAPSQ_VAR_O;
+  if (!sv && !ov) return KIND_EXIST;
+  if (!sv) return KIND_S_BOUND;
+  if (!ov) return KIND_O_BOUND;
+  return tp.s == tp.o ? KIND_SAME_VAR : KIND_TWO_VARS;
+}
+
+}  // namespace
+
+int validate_pattern(Ctx* ctx, const mapsq_pattern& tp) {
+  if (tp.var_mask & ~(MAPSQ_VAR_S | MAPSQ_VAR_P | MAPSQ_VAR_O))
+    return set_error(ctx, MAPSQ_ERR_INVALID, "var_mask 0x%x has unknown bits", tp.var_mask);
+  if (tp.var_mask & MAPSQ_VAR_P)
+    return set_error(ctx, MAPSQ_ERR_UNSUPPORTED, "variable predicates are not supported");
+  if ((tp.var_mask & MAPSQ_VAR_S) && tp.s >= MAPSQ_MAX_VARS)
+    return set_error(ctx, MAPSQ_ERR_INVALID, "variable id %u out of range", tp.s);
+  if ((tp.var_mask & MAPSQ_VAR_O) && tp.o >= MAPSQ_MAX_VARS)
+    return set_error(ctx, MAPSQ_ERR_INVALID, "variable id %u out of range", tp.o);
+  return MAPSQ_OK;
+}
+
+int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* out) {
+  const Store& st = ctx->store;
+  std::vector<RangeQuery> q(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const mapsq_pattern& tp = tps[i];
+    RangeQuery r{};
+    auto it = std::lower_bound(st.pred_id.begin(), st.pred_id.end(), tp.p);
+    if (it == st.pred_id.end() || *it != tp.p) {
+      r.kind = KIND_NONE;
+    } else {
+      size_t k = size_t(it - st.pred_id.begin());
+      r.b = st.pred_begin[k];
+      r.e = st.pred_begin[k + 1];
+      r.kind = pattern_kind(tp);
+      r.v0 = tp.s;
+      r.v1 = tp.o;
+    }
+    q[i] = r;
+  }
+  Scratch scratch(ctx);
+  RangeQuery* dq = nullptr;
+  uint64_t* dout = nullptr;
+  MQ_TRY(scratch.get(n, &dq));
+  MQ_TRY(scratch.get(2 * size_t(n), &dout));
+  MQ_CUDA(cudaMemcpyAsync(dq, q.data(), n * sizeof(RangeQuery), cudaMemcpyHostToDevice, ctx->stream));
+  StoreCols sc{st.so_s, st.so_o, st.os_o, st.os_s};
+  int rec = prof_begin(ctx, K_SCAN_RANGES);
+  scan_ranges_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(dq, n, sc, dout);
+  ++ctx->launches;
+  prof_end(ctx, rec, double(n) * 32);
+  MQ_CUDA(cudaGetLastError());
+  std::vector<uint64_t> h(2 * size_t(n));
+  MQ_CUDA(cudaMemcpyAsync(h.data(), dout, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (uint32_t i = 0; i < n; ++i) {
+    out[i].lo = h[2 * i];
+    out[i].hi = h[2 * i + 1];
+    out[i].kind = q[i].kind;
+    out[i].order = q[i].kind == KIND_O_BOUND ? 1 : q[i].kind == KIND_NONE ? -1 : 0;
+  }
+  return MAPSQ_OK;
+}
+
+int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImpl** out) {
+  const Store& st = ctx->store;
+  int32_t vars[2];
+  uint32_t nv = 0;
+  if (tp.var_mask & MAPSQ_VAR_S) vars[nv++] = int32_t(tp.s);
+  if ((tp.var_mask & MAPSQ_VAR_O) && !(nv == 1 && vars[0] == int32_t(tp.o))) vars[nv++] = int32_t(tp.o);
+  uint64_t rows = r.hi - r.lo;
+  TableImpl* t = nullptr;
+  switch (r.kind) {
+    case KIND_NONE:
+      MQ_TRY(table_alloc(ctx, 0, nv, vars, &t));
+      break;
+    case KIND_EXIST:
+      MQ_TRY(table_alloc(ctx, rows, 0, vars, &t));
+      break;
+    case KIND_S_BOUND:
+      MQ_TRY(table_alloc(ctx, rows, 1, vars, &t));
+      if (copy_u32(ctx, t->pub.col[0], st.so_o + r.lo, rows) != MAPSQ_OK) { table_release(ctx, t); return MAPSQ_ERR_CUDA; }
+      break;
+    case KIND_O_BOUND:
+      MQ_TRY(table_alloc(ctx, rows, 1, vars, &t));
+      if (copy_u32(ctx, t->pub.col[0], st.os_s + r.lo, rows) != MAPSQ_OK) { table_release(ctx, t); return MAPSQ_ERR_CUDA; }
+      break;
+    case KIND_TWO_VARS:
+      MQ_TRY(table_alloc(ctx, rows, 2, vars, &t));
+      if (copy_u32(ctx, t->pub.col[0], st.so_s + r.lo, rows) != MAPSQ_OK ||
+          copy_u32(ctx, t->pub.col[1], st.so_o + r.lo, rows) != MAPSQ_OK) {
+        table_release(ctx, t);
+        return MAPSQ_ERR_CUDA;
+      }
+      break;
+    case KIND_SAME_VAR: {
+      Scratch scratch(ctx);
+      uint32_t* flag = nullptr;
+      uint64_t* pos = nullptr;
+      MQ_TRY(scratch.get(rows + 1, &flag));
+      MQ_TRY(scratch.get(rows + 1, &pos));
+      unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(rows, 256), 152ull * 16)));
+      int rec = prof_begin(ctx, K_SCAN_FILTER);
+      if (rows) { same_var_flags_kernel<<<grid, 256, 0, ctx->stream>>>(st.so_s + r.lo, st.so_o + r.lo, rows, flag); ++ctx->launches; }
+      prof_end(ctx, rec, double(rows) * 12);
+      MQ_TRY(prefix_sum_u32_u64(ctx, flag, pos, rows));
+      uint64_t m = 0;
+      MQ_TRY(read_u64(ctx, pos + rows, &m, 1));
+      MQ_TRY(table_alloc(ctx, m, 1, vars, &t));
+      rec = prof_begin(ctx, K_SCAN_FILTER);
+      if (rows) { same_var_compact_kernel<<<grid, 256, 0, ctx->stream>>>(st.so_s + r.lo, rows, flag, pos, t->pub.col[0]); ++ctx->launches; }
+      prof_end(ctx, rec, double(rows) * 8 + double(m) * 4);
+      MQ_CUDA(cudaGetLastError());
+      break;
+    }
+    default:
+      return set_error(ctx, MAPSQ_ERR_INVALID, "bad pattern kind %d", r.kind);
+  }
+  *out = t;
+  return MAPSQ_OK;
+}
+
+}  // namespace mapsq

@@ -1,0 +1,374 @@
+"""Python binding of libmapsq (ctypes): argument marshalling only.
+
+Every function named ``mapsq_*`` here calls the C entry point of the same name
+declared in ``include/mapsq.h`` and raises :class:`MapsqError` on a negative
+status.  :class:`Context` and :class:`TableRef` are thin conveniences over
+them.  All device work happens in the library's CUDA kernels; there is no
+fallback: if ``libmapsq.so`` is missing or cannot be loaded, importing the
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmapsq.so")
+
+MAX_VARS = 16
+VAR_S, VAR_P, VAR_O = 1, 2, 4
+JOIN_AUTO, JOIN_HASH = 0, 1
+
+STATUS = {
+    0: "OK", -1: "INVALID", -2: "UNSUPPORTED", -3: "OOM", -4: "BUDGET",
+    -5: "CUDA", -6: "TIMEOUT", -7: "BUSY", -8: "NOT_FOUND",
+}
+
+
+class MapsqError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{STATUS.get(code, code)}: {message}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class Pattern(C.Structure):
+    _fields_ = [("s", C.c_uint32), ("p", C.c_uint32), ("o", C.c_uint32), ("var_mask", C.c_uint32)]
+
+
+class Table(C.Structure):
+    _fields_ = [("nrows", C.c_uint64), ("ncols", C.c_uint32), ("var", C.c_int32 * MAX_VARS),
+                ("col", C.c_void_p * MAX_VARS), ("on_device", C.c_int32)]
+
+
+class JoinOpts(C.Structure):
+    _fields_ = [("algorithm", C.c_int32), ("block_threads", C.c_int32), ("tile_rows", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_uint64), ("device_ms", C.c_double),
+                ("alg_bytes", C.c_double)]
+
+
+_P = C.c_void_p
+_TP = C.POINTER(Table)
+_SIGNATURES = {
+    "mapsq_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(Allocator), _P, C.c_uint64]),
+    "mapsq_destroy": (C.c_int, [_P]),
+    "mapsq_set_stream": (C.c_int, [_P, _P]),
+    "mapsq_last_error": (C.c_char_p, [_P]),
+    "mapsq_strerror": (C.c_char_p, [C.c_int]),
+    "mapsq_load_triples": (C.c_int, [_P, _P, _P, _P, C.c_uint64, C.c_int]),
+    "mapsq_store_info": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
+    "mapsq_scan_pattern": (C.c_int, [_P, C.POINTER(Pattern), C.POINTER(_TP)]),
+    "mapsq_join": (C.c_int, [_P, _TP, _TP, C.POINTER(_TP), C.POINTER(JoinOpts)]),
+    "mapsq_query": (C.c_int, [_P, C.POINTER(Pattern), C.c_uint32, C.POINTER(_TP)]),
+    "mapsq_table_from_columns": (C.c_int, [_P, C.c_uint64, C.c_uint32, C.POINTER(C.c_int32), C.POINTER(_P), C.c_int,
+                                           C.POINTER(_TP)]),
+    "mapsq_table_to_host": (C.c_int, [_P, _TP, C.POINTER(_P)]),
+    "mapsq_table_free": (None, [_P, _TP]),
+    "mapsq_sync": (C.c_int, [_P]),
+    "mapsq_memory_in_use": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    "mapsq_set_profiling": (C.c_int, [_P, C.c_int]),
+    "mapsq_kernel_stats": (C.c_int, [_P, C.POINTER(KernelStat), C.c_uint32, C.POINTER(C.c_uint32)]),
+    "mapsq_reset_stats": (C.c_int, [_P]),
+    "mapsq_launch_count": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libmapsq (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1702_03484_gb300.build.build()")
+        handle = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = lib().mapsq_last_error(ctx).decode() if ctx else lib().mapsq_strerror(rc).decode()
+        raise MapsqError(rc, msg)
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert isinstance(x, np.ndarray) and x.flags.c_contiguous
+    return x.ctypes.data
+
+
+def _is_device(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+# ------------------------------------------------------------------ entry points
+
+def mapsq_create(device=0, allocator=None, stream=None, budget=0):
+    ctx = _P()
+    _check(None, lib().mapsq_create(C.byref(ctx), device, C.byref(allocator) if allocator else None, stream, budget))
+    return ctx
+
+
+def mapsq_destroy(ctx):
+    _check(None, lib().mapsq_destroy(ctx))
+
+
+def mapsq_set_stream(ctx, stream):
+    _check(ctx, lib().mapsq_set_stream(ctx, stream))
+
+
+def mapsq_strerror(code):
+    return lib().mapsq_strerror(code).decode()
+
+
+def mapsq_last_error(ctx):
+    return lib().mapsq_last_error(ctx).decode()
+
+
+def mapsq_load_triples(ctx, s, p, o):
+    n = int(s.shape[0])
+    dev = _is_device(s)
+    if not dev:
+        s, p, o = (np.ascontiguousarray(x, dtype=np.uint32) for x in (s, p, o))
+    _check(ctx, lib().mapsq_load_triples(ctx, _ptr(s), _ptr(p), _ptr(o), n, 1 if dev else 0))
+
+
+def mapsq_store_info(ctx):
+    n, k = C.c_uint64(), C.c_uint32()
+    _check(ctx, lib().mapsq_store_info(ctx, C.byref(n), C.byref(k)))
+    return n.value, k.value
+
+
+def _pattern(tp):
+    return Pattern(*(int(x) for x in tp))
+
+
+def mapsq_scan_pattern(ctx, tp):
+    out = _TP()
+    _check(ctx, lib().mapsq_scan_pattern(ctx, C.byref(_pattern(tp)), C.byref(out)))
+    return out
+
+
+def mapsq_join(ctx, left, right, opts=None):
+    out = _TP()
+    _check(ctx, lib().mapsq_join(ctx, left, right, C.byref(out), C.byref(opts) if opts else None))
+    return out
+
+
+def mapsq_query(ctx, bgp):
+    arr = (Pattern * len(bgp))(*[_pattern(tp) for tp in bgp])
+    out = _TP()
+    _check(ctx, lib().mapsq_query(ctx, arr, len(bgp), C.byref(out)))
+    return out
+
+
+def mapsq_table_from_columns(ctx, vars_, cols, nrows=None):
+    ncols = len(vars_)
+    if nrows is None:
+        nrows = int(cols[0].shape[0]) if ncols else 0
+    dev = ncols > 0 and _is_device(cols[0])
+    if not dev:
+        cols = [np.ascontiguousarray(c, dtype=np.uint32) for c in cols]
+    var_arr = (C.c_int32 * max(ncols, 1))(*vars_)
+    col_arr = (_P * max(ncols, 1))(*[_ptr(c) for c in cols])
+    out = _TP()
+    _check(ctx, lib().mapsq_table_from_columns(ctx, nrows, ncols, var_arr, col_arr, 1 if dev else 0, C.byref(out)))
+    return out
+
+
+def mapsq_table_to_host(ctx, t):
+    tab = t.contents
+    cols = [np.empty(tab.nrows, dtype=np.uint32) for _ in range(tab.ncols)]
+    arr = (_P * max(tab.ncols, 1))(*[c.ctypes.data for c in cols])
+    _check(ctx, lib().mapsq_table_to_host(ctx, t, arr))
+    return list(tab.var[: tab.ncols]), cols
+
+
+def mapsq_table_free(ctx, t):
+    lib().mapsq_table_free(ctx, t)
+
+
+def mapsq_sync(ctx):
+    _check(ctx, lib().mapsq_sync(ctx))
+
+
+def mapsq_memory_in_use(ctx):
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(ctx, lib().mapsq_memory_in_use(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def mapsq_set_profiling(ctx, enable):
+    _check(ctx, lib().mapsq_set_profiling(ctx, 1 if enable else 0))
+
+
+def mapsq_kernel_stats(ctx):
+    cap = 64
+    arr = (KernelStat * cap)()
+    n = C.c_uint32()
+    _check(ctx, lib().mapsq_kernel_stats(ctx, arr, cap, C.byref(n)))
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "device_ms": arr[i].device_ms,
+                                   "alg_bytes": arr[i].alg_bytes} for i in range(min(n.value, cap))}
+
+
+def mapsq_reset_stats(ctx):
+    _check(ctx, lib().mapsq_reset_stats(ctx))
+
+
+def mapsq_launch_count(ctx):
+    n = C.c_uint64()
+    _check(ctx, lib().mapsq_launch_count(ctx, C.byref(n)))
+    return n.value
+
+
+# ------------------------------------------------------------------ conveniences
+
+class _CudaArray:
+    """Exposes one device column through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<u4", "data": (int(ptr or 0), False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+class TableRef:
+    """A table owned by the library, freed with its context or by :meth:`free`."""
+
+    def __init__(self, ctx: "Context", ptr):
+        self.ctx = ctx
+        self.ptr = ptr
+
+    @property
+    def nrows(self) -> int:
+        return int(self.ptr.contents.nrows)
+
+    @property
+    def vars(self):
+        t = self.ptr.contents
+        return list(t.var[: t.ncols])
+
+    def to_host(self):
+        """(vars, [numpy uint32 column, ...])"""
+        return mapsq_table_to_host(self.ctx.handle, self.ptr)
+
+    def device_columns(self):
+        """Zero-copy torch views of the device columns (valid until free)."""
+        import torch
+        t = self.ptr.contents
+        return [torch.as_tensor(_CudaArray(t.col[c], t.nrows), device="cuda") for c in range(t.ncols)]
+
+    def free(self):
+        if self.ptr:
+            mapsq_table_free(self.ctx.handle, self.ptr)
+            self.ptr = None
+
+
+class Context:
+    """One library context on one GPU; its device work runs on ``stream``
+    (default: torch's current stream when torch has a GPU, else a private one)."""
+
+    def __init__(self, device=0, stream=None, budget=0, allocator=None):
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    # torch's default stream is the legacy default stream (handle 1 for the runtime)
+                    stream = torch.cuda.current_stream(device).cuda_stream or 1
+            except ImportError:
+                pass
+        self._allocator = allocator
+        self.handle = mapsq_create(device, allocator, stream, budget)
+
+    def close(self):
+        if self.handle:
+            mapsq_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load_triples(self, s, p, o):
+        mapsq_load_triples(self.handle, s, p, o)
+
+    def store_info(self):
+        return mapsq_store_info(self.handle)
+
+    def scan_pattern(self, tp) -> TableRef:
+        return TableRef(self, mapsq_scan_pattern(self.handle, tp))
+
+    def join(self, left: TableRef, right: TableRef, opts=None) -> TableRef:
+        return TableRef(self, mapsq_join(self.handle, left.ptr, right.ptr, opts))
+
+    def query(self, bgp) -> TableRef:
+        return TableRef(self, mapsq_query(self.handle, bgp))
+
+    def table(self, vars_, cols, nrows=None) -> TableRef:
+        return TableRef(self, mapsq_table_from_columns(self.handle, list(vars_), list(cols), nrows))
+
+    def sync(self):
+        mapsq_sync(self.handle)
+
+    def memory_in_use(self):
+        return mapsq_memory_in_use(self.handle)
+
+    def set_profiling(self, on: bool):
+        mapsq_set_profiling(self.handle, on)
+
+    def kernel_stats(self):
+        return mapsq_kernel_stats(self.handle)
+
+    def reset_stats(self):
+        mapsq_reset_stats(self.handle)
+
+    def launch_count(self):
+        return mapsq_launch_count(self.handle)
+
+
+def torch_allocator():
+    """An allocator that takes device memory from torch's caching allocator."""
+    import torch
+
+    sizes = {}
+
+    def _alloc(nbytes, user, stream):
+        try:
+            p = torch.cuda.caching_allocator_alloc(int(nbytes))
+        except RuntimeError:
+            return None
+        sizes[p] = nbytes
+        return p
+
+    def _free(ptr, nbytes, user, stream):
+        sizes.pop(ptr, None)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = Allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    a._keep = (_alloc, _free, sizes)
+    return a

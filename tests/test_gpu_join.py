@@ -1,0 +1,190 @@
+"""GPU parity of mapsq_join against the CPU oracle (bit-exact multisets)."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from gpu_helpers import assert_same_multiset, device_table, join_and_check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_1702_03484_gb300 import Context
+    assert torch.cuda.is_available()
+    c = Context(device=0)
+    yield c
+    c.close()
+
+
+def test_pairwise_uniform_full_size(ctx):
+    """Tp1 16384 rows joined with Tp2 8192 rows on a key over 4096 ids."""
+    L, R = gen.pairwise_uniform(seed=1)
+    n = join_and_check(ctx, L, R, "pairwise uniform")
+    assert n > 30000
+
+
+def test_worked_example_table1(ctx):
+    from golden_example import Dictionary, load
+    g = load()
+    d = Dictionary()
+    tp1 = gen.Table([0, 1], [np.array([d.id(r[i]) for r in g["Tp1"]], np.uint32) for i in range(2)])
+    tp2 = gen.Table([0, 2], [np.array([d.id(r[i]) for r in g["Tp2"]], np.uint32) for i in range(2)])
+    out = ctx.join(device_table(ctx, tp1), device_table(ctx, tp2))
+    vars_, cols = out.to_host()
+    assert vars_ == [0, 1, 2]
+    rows = sorted(tuple(d.term(c[i]) for c in cols) for i in range(out.nrows))
+    assert rows == sorted(tuple(r) for r in g["RS"])
+
+
+def _random_pair(seed, n_shared, max_rows):
+    r = gen.Rng(seed, 21)
+    nl = int(r.below(1, max_rows + 1)[0])
+    nr = int(r.below(1, max_rows + 1)[0])
+    dom = int(r.between(1, 1, max(2, max_rows // 4))[0])
+    lv = list(range(n_shared)) + [8 + i for i in range(int(r.between(1, 0, 3)[0]))]
+    rv = list(range(n_shared)) + [12 + i for i in range(int(r.between(1, 0, 3)[0]))]
+    lv = lv or [8]
+    rv = rv or [12]
+    lv = [lv[i] for i in r.permutation(len(lv))]
+    rv = [rv[i] for i in r.permutation(len(rv))]
+    return gen.random_table(r, nl, lv, dom), gen.random_table(r, nr, rv, dom)
+
+
+@pytest.mark.parametrize("n_shared", [0, 1, 2])
+def test_random_joins_ragged(ctx, n_shared):
+    """Random sizes (ragged tails, several write tiles), shuffled column orders."""
+    max_rows = 300 if n_shared == 0 else 6000
+    for seed in range(25):
+        L, R = _random_pair(seed * 3 + n_shared, n_shared, max_rows)
+        join_and_check(ctx, L, R, f"seed {seed} shared {n_shared}")
+
+
+def test_extreme_ids_and_sentinel_key(ctx):
+    big = 0xFFFFFFFF
+    L = gen.Table([0, 1, 2], [np.array([big, big, 0, 5, big], np.uint32), np.array([big, 0, 0, 5, big], np.uint32),
+                              np.arange(5, dtype=np.uint32)])
+    R = gen.Table([1, 0, 3], [np.array([big, 0, big, 5], np.uint32), np.array([big, 0, big, 5], np.uint32),
+                              np.array([7, 8, 9, 10], np.uint32)])
+    join_and_check(ctx, L, R, "two-variable key with all-ones ids")
+    L1 = gen.Table([0, 1], [np.array([big, 0, big], np.uint32), np.array([1, 2, 3], np.uint32)])
+    R1 = gen.Table([0, 2], [np.array([0, big], np.uint32), np.array([4, 5], np.uint32)])
+    join_and_check(ctx, L1, R1, "one-variable key with ids 0 and 2^32-1")
+
+
+def test_hot_key_on_build_side(ctx):
+    """One key holds most of the smaller side: its group spans many output tiles."""
+    r = gen.Rng(5)
+    rk = np.concatenate((np.full(3000, 7, np.uint32), r.below(1000, 50).astype(np.uint32)))
+    R = gen.Table([0, 2], [rk, r.u32(rk.shape[0])])
+    lk = np.concatenate((np.full(40, 7, np.uint32), r.below(9000, 50).astype(np.uint32)))
+    L = gen.Table([0, 1], [lk, r.u32(lk.shape[0])])
+    n = join_and_check(ctx, L, R, "hot key")
+    assert n >= 40 * 3000
+
+
+def test_build_side_either_way(ctx):
+    r = gen.Rng(6)
+    small = gen.Table([0, 1, 3], [r.below(100, 64).astype(np.uint32), r.u32(100), r.u32(100)])
+    large = gen.Table([4, 0], [r.u32(5000), r.below(5000, 64).astype(np.uint32)])
+    join_and_check(ctx, small, large, "left smaller")
+    join_and_check(ctx, large, small, "right smaller")
+
+
+def test_cross_product_unit_and_empty(ctx):
+    r = gen.Rng(8)
+    A = gen.Table([0, 1], [r.u32(123), r.u32(123)])
+    B = gen.Table([2], [r.u32(77)])
+    join_and_check(ctx, A, B, "cross product")
+    join_and_check(ctx, A, gen.Table.unit(1), "unit table")
+    join_and_check(ctx, gen.Table.unit(1), A, "unit table on the left")
+    join_and_check(ctx, A, gen.Table.unit(0), "empty 0-column table")
+    E = gen.Table([0, 5], [np.zeros(0, np.uint32), np.zeros(0, np.uint32)])
+    join_and_check(ctx, A, E, "empty right")
+    join_and_check(ctx, E, A, "empty left")
+    join_and_check(ctx, gen.Table.unit(1), gen.Table.unit(1), "unit x unit")
+
+
+def test_disjoint_keys_give_empty(ctx):
+    A = gen.Table([0, 1], [np.arange(100, dtype=np.uint32), np.arange(100, dtype=np.uint32)])
+    B = gen.Table([0, 2], [np.arange(100, 200, dtype=np.uint32), np.arange(100, dtype=np.uint32)])
+    assert join_and_check(ctx, A, B, "disjoint") == 0
+
+
+def test_skewed_two_key_reduced(ctx):
+    """The skewed large-join workload at 2^18 x 2^16 rows: exactly 4 * 2^18 output rows."""
+    A, B = gen.skewed_two_key(seed=3, log_a=18, log_b=16, log_keys=14)
+    assert join_and_check(ctx, A, B, "skewed two-key") == 4 << 18
+
+
+def test_uneven_batch_reduced(ctx):
+    for i, (L, R, s) in enumerate(gen.uneven_batch(seed=4, n_joins=10, log_lo=8.0, log_hi=15.0)):
+        join_and_check(ctx, L, R, f"batch join {i} (s={s})")
+
+
+def test_result_tables_chain(ctx):
+    """A join result is a valid input of the next join (three-way chain)."""
+    r = gen.Rng(9)
+    A = gen.Table([0, 1], [r.below(500, 40).astype(np.uint32), r.below(500, 40).astype(np.uint32)])
+    B = gen.Table([1, 2], [r.below(400, 40).astype(np.uint32), r.below(400, 40).astype(np.uint32)])
+    C = gen.Table([2, 0], [r.below(300, 40).astype(np.uint32), r.below(300, 40).astype(np.uint32)])
+    ab = ctx.join(device_table(ctx, A), device_table(ctx, B))
+    abc = ctx.join(ab, device_table(ctx, C))
+    want = oracle.join_mapreduce(oracle.join_mapreduce(A, B), C)
+    assert_same_multiset(abc, want, "chain")
+
+
+def test_three_shared_variables_unsupported(ctx):
+    from paper_1702_03484_gb300 import MapsqError
+    A = gen.Table([0, 1, 2], [np.arange(4, dtype=np.uint32)] * 3)
+    with pytest.raises(MapsqError) as e:
+        ctx.join(device_table(ctx, A), device_table(ctx, A))
+    assert e.value.name == "UNSUPPORTED"
+
+
+def test_budget_and_allocator_failures():
+    import torch
+    from paper_1702_03484_gb300 import Context, MapsqError, mapsq
+    L, R = gen.pairwise_uniform(seed=1)
+    with Context(device=0, budget=1 << 20) as small:
+        tl, tr = device_table(small, L), device_table(small, R)
+        with pytest.raises(MapsqError) as e:
+            small.join(tl, tr)
+        assert e.value.name == "BUDGET"
+    calls = {"n": 0}
+
+    def refuse(nbytes, user, stream):
+        calls["n"] += 1
+        return None
+
+    def release(ptr, nbytes, user, stream):
+        pass
+
+    a = mapsq.Allocator(mapsq.ALLOC_FN(refuse), mapsq.FREE_FN(release), None)
+    a._keep = (refuse, release)
+    with pytest.raises(MapsqError) as e:
+        Context(device=0, allocator=a)
+    assert e.value.name == "OOM" and calls["n"] >= 1
+    torch.cuda.synchronize()
+
+
+def test_torch_caching_allocator():
+    from paper_1702_03484_gb300 import Context, torch_allocator
+    L, R = gen.pairwise_uniform(seed=1)
+    with Context(device=0, allocator=torch_allocator()) as c:
+        join_and_check(c, L, R, "torch allocator")
+        assert c.memory_in_use()[1] > 0
+
+
+def test_profiling_reports_kernels(ctx):
+    L, R = gen.pairwise_uniform(seed=1)
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    join_and_check(ctx, L, R, "profiled")
+    stats = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    for k in ("hash_insert", "probe_count", "prefix_sum", "join_write"):
+        assert stats[k]["launches"] >= 1 and stats[k]["device_ms"] > 0
+    assert stats["join_write"]["alg_bytes"] > 12 * 30000
