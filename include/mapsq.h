@@ -215,6 +215,39 @@ MAPSQ_API int mapsq_reset_stats(mapsq_ctx* ctx);
 /* Number of CUDA kernels this context has launched since it was created. */
 MAPSQ_API int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches);
 
+/* Join two tables without allocating any memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc (a host that
+ * owns all device memory and lends only fixed buffers, or a path where an
+ * allocation could block or fail).  It computes the same result as mapsq_join
+ * (same column layout) with no context: every intermediate lives in one
+ * 64 MiB device array inside the library, which each GPU that loads the
+ * library holds until the process exits.  Nothing is allocated: no cudaMalloc,
+ * no cudaFree, no allocating library routine.
+ *
+ * ``left``/``right``: caller-described tables, columns on the current device,
+ * 16-byte aligned.  The smaller input may have at most 262,144 rows and the
+ * larger at most 1,048,576; larger inputs give MAPSQ_ERR_INVALID before any
+ * device work.  ``out_cols``: one caller-owned device buffer per output column
+ * (shared variables, then the left table's other columns, then the right
+ * table's), each 16-byte aligned with room for ``out_capacity_rows`` rows.  On
+ * return ``*out_rows`` holds the join's row count; if it exceeds the capacity
+ * the call returns MAPSQ_ERR_BUDGET without writing the outputs, so the caller
+ * can retry with larger buffers.  On success ``*out`` describes the result
+ * (its columns are ``out_cols``; the caller keeps ownership).
+ *
+ * Work runs on ``cuda_stream`` (a cudaStream_t of the current device).  The
+ * call synchronises that stream once to read the row count; the output columns
+ * are complete when the stream's later work is.  The first call on a device
+ * also looks up the array's device address, so make it before any stream
+ * capture.  Every call shares the one array, and each call clears what must
+ * start at zero, so calls whose device work overlaps (on two streams or two
+ * threads) race and must be serialised by the caller.  Errors: INVALID (NULL,
+ * sizes beyond the limits, unaligned buffers), UNSUPPORTED (more than two
+ * shared variables), BUDGET (output larger than the capacity), CUDA, TIMEOUT. */
+MAPSQ_API int mapsq_join_noalloc(const mapsq_table* left, const mapsq_table* right, uint32_t* const* out_cols,
+                                 uint64_t out_capacity_rows, mapsq_table* out, uint64_t* out_rows,
+                                 void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

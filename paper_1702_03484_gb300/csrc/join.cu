@@ -19,6 +19,8 @@
 // table's other columns, then the right table's.  No shared variable: the cross
 // product, one key group holding every row.
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 #include "lookback.cuh"
@@ -485,4 +487,186 @@ int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const maps
   return MAPSQ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Join without any allocation, for callers that cannot call cudaMalloc.
+//
+// Some callers have no way to allocate device memory: code running inside a
+// host that owns all device memory and hands out only fixed buffers, code on a
+// path where an allocation could block or fail (a latency-critical loop, a
+// process past its memory quota), or code whose allocator the library cannot
+// reach.  mapsq_join_noalloc serves them: the caller passes the inputs and the
+// output buffers, and every intermediate of the hash join lives in one
+// file-scope device array of fixed size, kNoAllocScratchBytes, which each GPU
+// that loads this library holds until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+constexpr uint64_t kNoAllocMaxBuild = uint64_t(1) << 18;  // rows of the smaller input
+constexpr uint64_t kNoAllocMaxProbe = uint64_t(1) << 20;  // rows of the larger input
+constexpr int kNoAllocMaxDevices = 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The symbol's name
+// is only a host-side stand-in: the address must come from cudaGetSymbolAddress,
+// taken once per device with that device current.
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return MAPSQ_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MAPSQ_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return MAPSQ_OK;
+}
+
+struct SlotCounts {
+  const uint32_t* cnt;
+  __device__ __forceinline__ uint32_t operator()(uint64_t i) const { return cnt[i]; }
+};
+
+// Prefix sum of the hash slots' group sizes (group starts), scratch passed in.
+__global__ void __launch_bounds__(kLbThreads) noalloc_slot_prefix_kernel(const uint32_t* __restrict__ cnt, uint64_t n,
+                                                                         uint32_t* __restrict__ beg, uint64_t* lb,
+                                                                         uint32_t* err) {
+  SlotCounts v{cnt};
+  lookback_scan_tile<uint32_t>(v, n, beg, lb, err);
+}
+
+// Bump carving of the scratch array, 256-byte aligned regions.
+struct Carve {
+  unsigned char* base;
+  size_t used = 0;
+  template <class T>
+  T* take(uint64_t count) {
+    T* p = reinterpret_cast<T*>(base + used);
+    used += (size_t(count) * sizeof(T) + 255) & ~size_t(255);
+    return p;
+  }
+};
+
+}  // namespace
+
 }  // namespace mapsq
+
+using namespace mapsq;
+
+extern "C" int mapsq_join_noalloc(const mapsq_table* left, const mapsq_table* right, uint32_t* const* out_cols,
+                                  uint64_t out_capacity_rows, mapsq_table* out, uint64_t* out_rows,
+                                  void* cuda_stream) {
+  if (!left || !right || !out || !out_rows) return MAPSQ_ERR_INVALID;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  MQ_TRY(check_table(nullptr, left, "left"));
+  MQ_TRY(check_table(nullptr, right, "right"));
+  Layout lay;
+  MQ_TRY(make_layout(nullptr, left, right, &lay));
+  const bool build_left = left->nrows < right->nrows;
+  const mapsq_table* B = build_left ? left : right;
+  const mapsq_table* P = build_left ? right : left;
+  const int bside = build_left ? 0 : 1;
+  const int* bkey = build_left ? lay.lkey : lay.rkey;
+  const int* pkey = build_left ? lay.rkey : lay.lkey;
+  const uint64_t nb = B->nrows, np = P->nrows;
+  if (nb > kNoAllocMaxBuild || np > kNoAllocMaxProbe) return MAPSQ_ERR_INVALID;  // beyond the scratch array
+  if (lay.ncols && !out_cols) return MAPSQ_ERR_INVALID;
+  for (int c = 0; c < lay.ncols; ++c)
+    if (!out_cols[c] || (reinterpret_cast<uintptr_t>(out_cols[c]) & 15)) return MAPSQ_ERR_INVALID;
+
+  unsigned char* base = nullptr;
+  MQ_TRY(noalloc_scratch(&base));
+  Carve cv{base};
+  uint32_t* status = cv.take<uint32_t>(64);
+  const bool cross = lay.nkey == 0;
+  uint64_t T = 0;
+  uint64_t* off = nullptr;
+  uint32_t* pbeg = nullptr;
+  uint32_t* grouped[MAPSQ_MAX_VARS] = {};
+  if (nb == 0 || np == 0) {
+    T = 0;
+  } else if (cross) {
+    T = np * nb;  // both below 2^20: no overflow
+  } else {
+    KeyCols bk{B->col[bkey[0]], lay.nkey == 2 ? B->col[bkey[1]] : nullptr};
+    KeyCols pk{P->col[pkey[0]], lay.nkey == 2 ? P->col[pkey[1]] : nullptr};
+    const uint64_t M = std::max<uint64_t>(1024, 2 * nb);
+    Slot* tab = cv.take<Slot>(M + 1);
+    uint32_t* cnt = cv.take<uint32_t>(M + 2);
+    uint32_t* beg = cv.take<uint32_t>(M + 2);
+    uint32_t* slot_of = cv.take<uint32_t>(nb);
+    uint32_t* rank_of = cv.take<uint32_t>(nb);
+    ValueCols vc{};
+    for (int c = 0; c < lay.ncols; ++c) {
+      if (lay.side[c] != bside) continue;
+      grouped[c] = cv.take<uint32_t>(nb);
+      vc.src[vc.n] = B->col[lay.col[c]];
+      vc.dst[vc.n] = grouped[c];
+      ++vc.n;
+    }
+    pbeg = cv.take<uint32_t>(np);
+    off = cv.take<uint64_t>(np + 1);
+    uint64_t* lb_slots = cv.take<uint64_t>(lookback_scratch_words(M + 1));
+    uint64_t* lb_probe = cv.take<uint64_t>(lookback_scratch_words(np));
+    if (cv.used > kNoAllocScratchBytes) return MAPSQ_ERR_INVALID;
+    // every call starts from cleared state: the array keeps the previous call's contents
+    if (cudaMemsetAsync(status, 0, 64 * sizeof(uint32_t), stream) != cudaSuccess ||
+        cudaMemsetAsync(lb_slots, 0, lookback_scratch_words(M + 1) * sizeof(uint64_t), stream) != cudaSuccess ||
+        cudaMemsetAsync(lb_probe, 0, lookback_scratch_words(np) * sizeof(uint64_t), stream) != cudaSuccess)
+      return MAPSQ_ERR_CUDA;
+    hash_init_kernel<<<grid_for(M + 1, 152ull * 32), 256, 0, stream>>>(tab, cnt, M + 1);
+    hash_insert_kernel<<<grid_for(nb, 152ull * 32), 256, 0, stream>>>(bk, nb, tab, cnt, uint32_t(M), slot_of, rank_of,
+                                                                      status);
+    noalloc_slot_prefix_kernel<<<unsigned(ceil_div(M + 1, kLbTile)), kLbThreads, 0, stream>>>(cnt, M + 1, beg,
+                                                                                              lb_slots, status);
+    hash_finalize_kernel<<<grid_for(M + 1, 152ull * 32), 256, 0, stream>>>(tab, cnt, beg, M + 1);
+    if (vc.n) hash_scatter_kernel<<<grid_for(nb, 152ull * 32), 256, 0, stream>>>(vc, nb, slot_of, rank_of, beg);
+    probe_count_kernel<<<unsigned(ceil_div(np, kLbTile)), kLbThreads, 0, stream>>>(pk, np, tab, uint32_t(M), pbeg, off,
+                                                                                   lb_probe, status);
+    if (cudaGetLastError() != cudaSuccess) return MAPSQ_ERR_CUDA;
+    uint64_t host[2] = {0, 0};
+    if (cudaMemcpyAsync(&host[0], off + np, sizeof(uint64_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaMemcpyAsync(&host[1], status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return MAPSQ_ERR_CUDA;
+    if (host[1] & 2u) return MAPSQ_ERR_TIMEOUT;
+    if (host[1]) return MAPSQ_ERR_CUDA;
+    T = host[0];
+  }
+  *out_rows = T;
+  if (T > out_capacity_rows) return MAPSQ_ERR_BUDGET;
+  memset(out, 0, sizeof(*out));
+  out->nrows = T;
+  out->ncols = uint32_t(lay.ncols);
+  out->on_device = 1;
+  for (int c = 0; c < MAPSQ_MAX_VARS; ++c) out->var[c] = c < lay.ncols ? lay.var[c] : -1;
+  for (int c = 0; c < lay.ncols; ++c) out->col[c] = out_cols[c];
+  if (T && lay.ncols) {
+    WriteParams wp{};
+    wp.off = off;
+    wp.pbeg = pbeg;
+    wp.np = np;
+    wp.nb = nb;
+    wp.T = T;
+    wp.ncols = lay.ncols;
+    wp.cross = cross ? 1 : 0;
+    for (int c = 0; c < lay.ncols; ++c) {
+      const bool fb = lay.side[c] == bside && c >= lay.nkey;
+      wp.out[c] = out_cols[c];
+      if (fb) {
+        wp.src[c] = cross ? B->col[lay.col[c]] : grouped[c];
+        wp.from_build |= 1u << c;
+      } else {
+        wp.src[c] = P->col[c < lay.nkey ? pkey[c] : lay.col[c]];
+      }
+    }
+    unsigned grid = unsigned(std::min<uint64_t>(ceil_div(T, kWriteTile), 152ull * 8));
+    join_write_kernel<<<grid, kWriteThreads, 0, stream>>>(wp);
+    if (cudaGetLastError() != cudaSuccess) return MAPSQ_ERR_CUDA;
+  }
+  return MAPSQ_OK;
+}

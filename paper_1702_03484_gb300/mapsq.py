@@ -84,6 +84,7 @@ _SIGNATURES = {
     "mapsq_kernel_stats": (C.c_int, [_P, C.POINTER(KernelStat), C.c_uint32, C.POINTER(C.c_uint32)]),
     "mapsq_reset_stats": (C.c_int, [_P]),
     "mapsq_launch_count": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
+    "mapsq_join_noalloc": (C.c_int, [_TP, _TP, C.POINTER(_P), C.c_uint64, _TP, C.POINTER(C.c_uint64), _P]),
 }
 
 _lib = None
@@ -243,6 +244,33 @@ def mapsq_launch_count(ctx):
     n = C.c_uint64()
     _check(ctx, lib().mapsq_launch_count(ctx, C.byref(n)))
     return n.value
+
+
+def mapsq_join_noalloc(left, right, out_cols, capacity, stream=None):
+    """Join caller-described tables into caller-owned output buffers without any
+    allocation (see include/mapsq.h).  ``left``/``right`` are ``Table`` structs
+    (or pointers to them), ``out_cols`` device addresses.  Returns (status,
+    Table describing the result, row count); the status is not raised so that a
+    caller can retry with larger buffers after MAPSQ_ERR_BUDGET."""
+    cols = (_P * max(len(out_cols), 1))(*out_cols)
+    out = Table()
+    rows = C.c_uint64()
+    lp = left if isinstance(left, _TP) else C.pointer(left)
+    rp = right if isinstance(right, _TP) else C.pointer(right)
+    rc = lib().mapsq_join_noalloc(lp, rp, cols, capacity, C.pointer(out), C.byref(rows), stream)
+    return rc, out, rows.value
+
+
+def table_view(vars_, cols, nrows=None):
+    """A ``Table`` struct describing caller-owned device columns (no copy)."""
+    t = Table()
+    t.nrows = int(cols[0].shape[0]) if cols else int(nrows or 0)
+    t.ncols = len(vars_)
+    for c in range(MAX_VARS):
+        t.var[c] = vars_[c] if c < len(vars_) else -1
+        t.col[c] = _ptr(cols[c]) if c < len(cols) else None
+    t.on_device = 1
+    return t
 
 
 # ------------------------------------------------------------------ conveniences
