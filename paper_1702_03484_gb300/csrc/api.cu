@@ -12,7 +12,7 @@ const char* const kKernelNames[K_COUNT_KERNELS] = {
     "store_radix_histogram", "store_radix_scatter", "store_dedup", "store_predicate_heads",
     "scan_ranges",           "scan_emit",           "scan_filter", "prefix_sum",
     "hash_insert",           "hash_scatter",        "probe_count", "join_write",
-    "cross_write",           "copy"};
+    "cross_write",           "copy",        "hll_sketch",  "write_partition"};
 
 int set_error(Ctx* ctx, int code, const char* fmt, ...) {
   if (ctx) {
@@ -247,8 +247,8 @@ int mapsq_create(mapsq_ctx** out, int device, const mapsq_allocator* allocator, 
     uint64_t keep = UINT64_MAX;  // keep freed blocks cached in the pool
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
-  if (cudaMallocHost(&ctx->h_pinned, 64 * sizeof(uint64_t)) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
-  memset(ctx->h_pinned, 0, 64 * sizeof(uint64_t));
+  if (cudaMallocHost(&ctx->h_pinned, kPinnedWords * sizeof(uint64_t)) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
+  memset(ctx->h_pinned, 0, kPinnedWords * sizeof(uint64_t));
   void* st = nullptr;
   rc = dev_alloc(ctx, 256, &st);
   if (rc != MAPSQ_OK) return fail(rc);

@@ -13,6 +13,8 @@
 
 namespace mapsq {
 
+constexpr size_t kPinnedWords = 4096;
+
 // Kernels timed by the profiling switch (mapsq_set_profiling).
 enum KernelId {
   K_STORE_HIST = 0,
@@ -29,6 +31,8 @@ enum KernelId {
   K_JOIN_WRITE,
   K_CROSS_WRITE,
   K_COPY,
+  K_HLL,
+  K_PARTITION,
   K_COUNT_KERNELS
 };
 
@@ -85,7 +89,7 @@ struct mapsq_ctx {
   std::string err;
   mapsq::Store store;
   uint32_t* d_status = nullptr;    // device status word: 0 = fine
-  uint64_t* h_pinned = nullptr;    // small pinned buffer for device->host reads
+  uint64_t* h_pinned = nullptr;    // pinned buffer for device->host reads (kPinnedWords words)
   bool profiling = false;
   uint64_t launches = 0;          // kernels launched by this context
   std::vector<mapsq::LaunchRecord> pending;

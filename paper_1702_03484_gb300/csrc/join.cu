@@ -5,13 +5,15 @@
 // packed into 64 bits (one variable: the id; two: smaller variable id in the
 // high word), and keeps its other columns as its value (by row index).
 // Shuffle: the smaller table (the build side) is partitioned by key through an
-// open-addressing hash table: one insert pass gives each row its key group and
-// its rank inside the group (warp-aggregated atomics), a prefix sum over the
-// groups' sizes gives each group's start, and a scatter pass writes the build
-// side's value columns grouped by key.  Reduce: every row of the other table
-// (the probe side) looks its key up and counts its matches (the size of its
-// LEFT x RIGHT cross product); an exclusive prefix sum of the counts gives each
-// probe row its output range; the write pass then emits every LEFT x RIGHT pair
+// open-addressing hash table sized from a HyperLogLog estimate of its distinct
+// keys: one insert pass gives each row its key group and its rank inside the
+// group (warp-aggregated atomics), a prefix sum over the groups' sizes gives
+// each group's start, and a scatter pass writes the build side's value columns
+// grouped by key, row-major.  Reduce: every row of the other table (the probe
+// side) looks its key up and counts its matches (the size of its LEFT x RIGHT
+// cross product) inside a single-pass look-back prefix sum that gives each probe
+// row its output range; a partition pass finds, for every output tile, the
+// probe rows that feed it; the write pass then emits every LEFT x RIGHT pair
 // exactly once, partitioned by output position so that skewed keys are spread
 // over all SMs, with 16-byte streaming stores into each output column.
 //
@@ -19,6 +21,7 @@
 // table's other columns, then the right table's.  No shared variable: the cross
 // product, one key group holding every row.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -30,15 +33,29 @@ namespace mapsq {
 namespace {
 
 constexpr uint64_t kEmptyKey = ~0ull;
-constexpr int kWriteThreads = 256;
-constexpr int kWriteGroups = 4;                                     // 4-row groups per thread per tile
-constexpr int kWriteTile = kWriteThreads * kWriteGroups * 4;        // output rows per tile
-constexpr int kOffCache = 2048;                                     // offsets cached in shared memory
+constexpr uint32_t kNoSlot = 0xffffffffu;
+constexpr int kThreads = 256;                                        // threads per CTA of the probe and write passes
+constexpr int kProbeTile = 2048;                                     // probe rows per count tile
+constexpr int kProbeItems = kProbeTile / kThreads;                   // probe rows per thread
+constexpr int kWriteRows = 16;                                       // output rows per thread per write tile
+constexpr int kWriteTile = kThreads * kWriteRows;                    // output rows per write tile
+constexpr int kStageRows = 1800;                                     // probe rows staged per write tile (48 KB of static shared memory in all)
+constexpr int kMapWords = kWriteTile + kWriteTile / 32;              // row map, padded one word per 32
+constexpr int kHllBits = 12;
+constexpr int kHllRegs = 1 << kHllBits;
+constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;                 // smaller build sides size the table by rows
 
-struct __align__(16) Slot {
-  uint64_t key;
-  uint32_t cnt;
-  uint32_t beg;
+// Open-addressing table of the build side's distinct keys: ``keys`` holds M
+// 64-bit keys in buckets of 4 (one 32-byte sector), probed bucket after bucket
+// from the key's home bucket; ``group`` holds, per slot, the key group's size
+// and its first row in the grouped build values.  The all-ones key marks an
+// empty slot; the one real key equal to it uses the extra group entry M.
+constexpr int kBucket = 4;
+
+struct HashTable {
+  uint64_t* keys;  // M entries, M a multiple of kBucket
+  uint2* group;    // M + 1 entries: {count, begin}
+  uint32_t M;
 };
 
 struct KeyCols {
@@ -46,9 +63,11 @@ struct KeyCols {
   const uint32_t* c1;  // nullptr for a single-variable key
 };
 
+// Key columns are streamed once per pass: evict-first loads keep the hash table
+// resident in L2.
 __device__ __forceinline__ uint64_t load_key(const KeyCols& k, uint64_t i) {
-  uint64_t a = k.c0[i];
-  return k.c1 ? (a << 32) | k.c1[i] : a;
+  uint64_t a = __ldcs(k.c0 + i);
+  return k.c1 ? (a << 32) | __ldcs(k.c1 + i) : a;
 }
 
 // MurmurHash3's 64-bit finaliser (Appleby), a bijective mix of the key bits.
@@ -61,53 +80,120 @@ __device__ __forceinline__ uint64_t mix_key(uint64_t k) {
   return k;
 }
 
-// Home slot in [0, M): multiply-shift range reduction of the mixed key.
-__device__ __forceinline__ uint32_t home_slot(uint64_t key, uint32_t M) {
-  return uint32_t(((mix_key(key) >> 32) * uint64_t(M)) >> 32);
+// Home bucket in [0, M / kBucket): Fibonacci (multiplicative) hashing of the
+// key, folded to 32 bits, then multiply-shift range reduction.
+__device__ __forceinline__ uint32_t home_bucket(uint64_t key, uint32_t M) {
+  const uint32_t h = uint32_t((key * 0x9e3779b97f4a7c15ull) >> 32) ^ uint32_t(key >> 29);
+  return uint32_t((uint64_t(h * 0x85ebca6bu) * uint64_t(M / kBucket)) >> 32);
 }
 
-__global__ void hash_init_kernel(Slot* __restrict__ tab, uint32_t* __restrict__ cnt, uint64_t nslots) {
-  for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < nslots; j += uint64_t(gridDim.x) * blockDim.x) {
-    tab[j] = Slot{kEmptyKey, 0u, 0u};
-    cnt[j] = 0u;
+// Slot of ``key`` in the table, or kNoSlot, starting from its home bucket
+// whose keys are already loaded (k01 = slots 0-1, k23 = slots 2-3).
+__device__ __forceinline__ uint32_t find_slot(const HashTable& t, uint64_t key, uint32_t b, ulonglong2 k01,
+                                              ulonglong2 k23) {
+  if (key == kEmptyKey) return t.M;
+  const uint32_t nbk = t.M / kBucket;
+  for (uint32_t it = 0; it < nbk; ++it) {
+    // first slot of the bucket holding the key or empty decides
+    const uint32_t hit = uint32_t(k01.x == key) | uint32_t(k01.y == key) << 1 | uint32_t(k23.x == key) << 2 |
+                         uint32_t(k23.y == key) << 3;
+    const uint32_t emp = uint32_t(k01.x == kEmptyKey) | uint32_t(k01.y == kEmptyKey) << 1 |
+                         uint32_t(k23.x == kEmptyKey) << 2 | uint32_t(k23.y == kEmptyKey) << 3;
+    if (hit | emp) {
+      const int j = __ffs(hit | emp) - 1;
+      return (hit >> j) & 1u ? b * kBucket + j : kNoSlot;
+    }
+    b = b + 1 == nbk ? 0 : b + 1;
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.keys + uint64_t(b) * kBucket);
+    k01 = __ldg(p);
+    k23 = __ldg(p + 1);
   }
+  return kNoSlot;
+}
+
+__device__ __forceinline__ void load_bucket(const HashTable& t, uint64_t key, uint32_t* b, ulonglong2* k01,
+                                            ulonglong2* k23) {
+  *b = home_bucket(key, t.M);
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.keys + uint64_t(*b) * kBucket);
+  *k01 = __ldg(p);
+  *k23 = __ldg(p + 1);
+}
+
+// HyperLogLog sketch of the build keys (Flajolet, Fusy, Gandouet, Meunier,
+// 2007): 2^12 registers hold the largest leading-zero count + 1 seen among the
+// hashes routed to them.  The input is salted so the hash is independent of the
+// table's.
+__global__ void hll_kernel(KeyCols k, uint64_t n, uint32_t* __restrict__ regs) {
+  __shared__ uint32_t s[kHllRegs];
+  for (int j = threadIdx.x; j < kHllRegs; j += blockDim.x) s[j] = 0;
+  __syncthreads();
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t h = mix_key(load_key(k, i) ^ 0x9e3779b97f4a7c15ull);
+    uint32_t idx = uint32_t(h >> (64 - kHllBits));
+    uint64_t w = (h << kHllBits) | (1ull << (kHllBits - 1));
+    atomicMax(&s[idx], uint32_t(__clzll(w) + 1));
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kHllRegs; j += blockDim.x)
+    if (s[j]) atomicMax(&regs[j], s[j]);
+}
+
+double hll_estimate(const uint32_t* regs) {
+  const double m = kHllRegs;
+  double sum = 0.0;
+  int zeros = 0;
+  for (int j = 0; j < kHllRegs; ++j) {
+    sum += std::ldexp(1.0, -int(regs[j]));
+    zeros += regs[j] == 0;
+  }
+  double e = (0.7213 / (1.0 + 1.079 / m)) * m * m / sum;
+  if (e <= 2.5 * m && zeros > 0) e = m * std::log(m / zeros);  // small-range correction (linear counting)
+  return e;
 }
 
 // Insert every build row's key; slot_of[i] = its group's slot, rank_of[i] = its
-// rank inside the group.  The key equal to the empty marker lives in slot M.
-__global__ void hash_insert_kernel(KeyCols bk, uint64_t nb, Slot* __restrict__ tab, uint32_t* __restrict__ cnt,
-                                   uint32_t M, uint32_t* __restrict__ slot_of, uint32_t* __restrict__ rank_of,
-                                   uint32_t* __restrict__ status) {
+// rank inside the group, counted in the group table.
+__global__ void hash_insert_kernel(KeyCols bk, uint64_t nb, HashTable t, uint32_t* __restrict__ slot_of,
+                                   uint32_t* __restrict__ rank_of, uint32_t* __restrict__ status) {
   const unsigned lane = threadIdx.x & 31;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint32_t nbk = t.M / kBucket;
   for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x; base < nb; base += stride) {
     uint64_t i = base + threadIdx.x;
     bool valid = i < nb;
-    uint32_t s = 0xffffffffu;
+    uint32_t s = kNoSlot;
     if (valid) {
-      uint64_t key = load_key(bk, i);
+      const uint64_t key = load_key(bk, i);
       if (key == kEmptyKey) {
-        s = M;
+        s = t.M;
       } else {
-        uint32_t h = home_slot(key, M);
-        for (uint32_t probe = 0; probe < M; ++probe) {
-          uint64_t k = *reinterpret_cast<volatile uint64_t*>(&tab[h].key);
-          if (k == key) { s = h; break; }
-          if (k == kEmptyKey) {
-            unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&tab[h].key),
-                                                (unsigned long long)kEmptyKey, (unsigned long long)key);
-            if (prev == kEmptyKey || prev == key) { s = h; break; }
+        uint32_t b = home_bucket(key, t.M);
+        for (uint32_t it = 0; it < nbk && s == kNoSlot; ++it) {
+          uint64_t* bkt = t.keys + uint64_t(b) * kBucket;
+          const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt));
+          const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt) + 1);
+          const uint64_t k[4] = {k01.x, k01.y, k23.x, k23.y};
+#pragma unroll
+          for (int j = 0; j < kBucket; ++j) {
+            if (s != kNoSlot) break;
+            if (k[j] == key) {
+              s = b * kBucket + j;
+            } else if (k[j] == kEmptyKey) {
+              const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(bkt + j),
+                                                        (unsigned long long)kEmptyKey, (unsigned long long)key);
+              if (prev == kEmptyKey || prev == key) s = b * kBucket + j;
+            }
           }
-          h = h + 1 == M ? 0 : h + 1;
+          b = b + 1 == nbk ? 0 : b + 1;
         }
-        if (s == 0xffffffffu) atomicOr(status, 1u);  // table full: the host retries larger
+        if (s == kNoSlot) atomicOr(status, 1u);  // table full: the host rebuilds it larger
       }
     }
     // warp-aggregated group ranks: one atomic per distinct slot in the warp
     unsigned peers = __match_any_sync(0xffffffffu, s);
     int leader = __ffs(peers) - 1;
     uint32_t base_rank = 0;
-    if (lane == unsigned(leader) && valid && s != 0xffffffffu) base_rank = atomicAdd(&cnt[s], __popc(peers));
+    if (lane == unsigned(leader) && valid && s != kNoSlot) base_rank = atomicAdd(&t.group[s].x, __popc(peers));
     base_rank = __shfl_sync(0xffffffffu, base_rank, leader);
     if (valid) {
       slot_of[i] = s;
@@ -116,174 +202,403 @@ __global__ void hash_insert_kernel(KeyCols bk, uint64_t nb, Slot* __restrict__ t
   }
 }
 
-__global__ void hash_finalize_kernel(Slot* __restrict__ tab, const uint32_t* __restrict__ cnt,
-                                     const uint32_t* __restrict__ beg, uint64_t nslots) {
-  for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < nslots; j += uint64_t(gridDim.x) * blockDim.x) {
-    uint32_t c = cnt[j];
-    if (c) {
-      tab[j].cnt = c;
-      tab[j].beg = beg[j];
+// Group starts: exclusive prefix sum of the groups' sizes, written next to
+// them (look-back scan over the M + 1 group entries).
+struct GroupCounts {
+  const uint2* group;
+  __device__ __forceinline__ void fill(uint64_t base, uint64_t n, uint64_t* s) const {
+#pragma unroll 4
+    for (int k = 0; k < kLbItems; ++k) {
+      const int local = k * kLbThreads + threadIdx.x;
+      const uint64_t row = base + local;
+      s[lb_pad(local)] = row < n ? uint64_t(group[row].x) : 0ull;
     }
   }
+};
+
+struct GroupStarts {
+  uint2* group;
+  __device__ __forceinline__ void store(uint64_t row, uint64_t v) const {
+    if (group[row].x) group[row].y = uint32_t(v);
+  }
+  __device__ __forceinline__ void total(uint64_t) const {}
+};
+
+__global__ void __launch_bounds__(kLbThreads) slot_prefix_kernel(uint2* __restrict__ group, uint64_t n, uint64_t* lb,
+                                                                 uint32_t* err) {
+  GroupCounts c{group};
+  GroupStarts s{group};
+  lookback_scan_tile(c, n, s, lb, err);
 }
 
-struct ValueCols {
+struct BuildValues {
   const uint32_t* src[MAPSQ_MAX_VARS];
-  uint32_t* dst[MAPSQ_MAX_VARS];
   int n;
 };
 
-// Group the build side's value columns by key: row i goes to beg[slot] + rank.
-__global__ void hash_scatter_kernel(ValueCols v, uint64_t nb, const uint32_t* __restrict__ slot_of,
-                                    const uint32_t* __restrict__ rank_of, const uint32_t* __restrict__ beg) {
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nb; i += uint64_t(gridDim.x) * blockDim.x) {
-    uint32_t pos = beg[slot_of[i]] + rank_of[i];
-    for (int c = 0; c < v.n; ++c) v.dst[c][pos] = v.src[c][i];
+constexpr int kScatterRows = 4;  // build rows per thread, loads issued together
+
+// Group the build side's value columns by key, row-major: row i's values go to
+// grouped[(begin of its group + rank) * n + j].
+__global__ void hash_scatter_kernel(BuildValues v, uint64_t nb, const uint32_t* __restrict__ slot_of,
+                                    const uint32_t* __restrict__ rank_of, const uint2* __restrict__ group,
+                                    uint32_t* __restrict__ grouped) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kScatterRows;
+  for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x * kScatterRows + threadIdx.x; base < nb; base += stride) {
+    uint32_t s[kScatterRows], rk[kScatterRows], beg[kScatterRows];
+#pragma unroll
+    for (int k = 0; k < kScatterRows; ++k) {
+      const uint64_t i = base + uint64_t(k) * blockDim.x;
+      s[k] = i < nb ? __ldcs(slot_of + i) : kNoSlot;
+      rk[k] = i < nb ? __ldcs(rank_of + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kScatterRows; ++k) beg[k] = s[k] != kNoSlot ? group[s[k]].y : 0u;
+    for (int c = 0; c < v.n; ++c) {
+      uint32_t x[kScatterRows];
+#pragma unroll
+      for (int k = 0; k < kScatterRows; ++k) {
+        const uint64_t i = base + uint64_t(k) * blockDim.x;
+        x[k] = s[k] != kNoSlot ? __ldcs(v.src[c] + i) : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < kScatterRows; ++k)
+        if (s[k] != kNoSlot) grouped[uint64_t(beg[k] + rk[k]) * uint32_t(v.n) + c] = x[k];
+    }
   }
 }
 
-// Count pass fused with the prefix sum: each probe row looks its key up, records
-// the start of its key group in pbeg and contributes its match count to a
-// single-pass scan that writes the probe rows' output offsets.
-struct ProbeCounts {
-  KeyCols pk;
-  const Slot* tab;
-  uint32_t M;
-  uint32_t* pbeg;
-  __device__ __forceinline__ uint32_t operator()(uint64_t i) const {
-    uint64_t key = load_key(pk, i);
-    uint32_t c = 0, b = 0;
-    if (key == kEmptyKey) {
-      Slot sl = tab[M];
-      c = sl.cnt;
-      b = sl.beg;
-    } else {
-      uint32_t h = home_slot(key, M);
-      for (uint32_t probe = 0; probe < M; ++probe) {
-        Slot sl = tab[h];
-        if (sl.key == key) {
-          c = sl.cnt;
-          b = sl.beg;
-          break;
-        }
-        if (sl.key == kEmptyKey) break;
-        h = h + 1 == M ? 0 : h + 1;
+// Probes ``kProbeItems`` rows per thread, four lookups in flight at a time:
+// out_cnt[k] / out_beg[k] = match count and group start of row
+// base + k * kThreads + threadIdx.x (0 past np).
+__device__ __forceinline__ void probe_rows(const KeyCols& pk, uint64_t np, const HashTable& t, uint64_t base,
+                                           uint32_t* out_cnt, uint32_t* out_beg) {
+  constexpr int H = 4;
+#pragma unroll
+  for (int h0 = 0; h0 < kProbeItems; h0 += H) {
+    uint64_t key[H];
+    uint32_t b[H], s[H];
+    ulonglong2 k01[H], k23[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const uint64_t row = base + uint64_t(h0 + k) * kThreads + threadIdx.x;
+      key[k] = row < np ? load_key(pk, row) : kEmptyKey;
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k)
+      if (key[k] != kEmptyKey) load_bucket(t, key[k], &b[k], &k01[k], &k23[k]);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const uint64_t row = base + uint64_t(h0 + k) * kThreads + threadIdx.x;
+      s[k] = row < np ? find_slot(t, key[k], b[k], k01[k], k23[k]) : kNoSlot;
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const uint2 g = s[k] != kNoSlot ? t.group[s[k]] : make_uint2(0u, 0u);
+      out_cnt[h0 + k] = g.x;
+      out_beg[h0 + k] = g.y;
+    }
+  }
+}
+
+// Count pass, tile-local: every probe row's match count and group start, the
+// exclusive prefix sums of the counts inside its tile of kProbeTile rows, and
+// the tile's total.  Output offsets are tile_base[row / kProbeTile] +
+// local[row] once the tile totals are scanned; no CTA waits for another.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(KeyCols pk, uint64_t np, HashTable t,
+                                                                  OffT* __restrict__ local,
+                                                                  uint32_t* __restrict__ pbeg,
+                                                                  uint64_t* __restrict__ tile_total,
+                                                                  uint32_t* __restrict__ status) {
+  __shared__ uint32_t s_cnt[kProbeTile + kProbeTile / 32];
+  __shared__ uint64_t s_warp[kThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t base = uint64_t(blockIdx.x) * kProbeTile;
+  auto pad = [](int i) { return i + (i >> 5); };
+  {
+    uint32_t cnt[kProbeItems], beg[kProbeItems];
+    probe_rows(pk, np, t, base, cnt, beg);
+#pragma unroll
+    for (int k = 0; k < kProbeItems; ++k) {
+      const int loc = k * kThreads + tid;
+      if (base + loc < np) __stcs(pbeg + base + loc, beg[k]);
+      s_cnt[pad(loc)] = cnt[k];
+    }
+  }
+  __syncthreads();
+  // block scan: each thread owns kProbeItems consecutive rows
+  uint32_t v[kProbeItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kProbeItems; ++k) {
+    v[k] = s_cnt[pad(tid * kProbeItems + k)];
+    sum += v[k];
+  }
+  uint64_t inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint64_t x = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += x;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  uint64_t run = inc - sum, tile_sum = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) {
+    const uint64_t x = s_warp[w];
+    if (w < warp) run += x;
+    tile_sum += x;
+  }
+  // local offsets, written back in row order through shared memory, half a tile at a time
+  __syncthreads();
+  uint64_t* s_off = reinterpret_cast<uint64_t*>(s_cnt);
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    if ((tid * kProbeItems) / (kProbeTile / 2) == half) {
+#pragma unroll
+      for (int k = 0; k < kProbeItems; ++k) {
+        s_off[(tid * kProbeItems + k) % (kProbeTile / 2)] = run;
+        run += v[k];
       }
     }
-    pbeg[i] = b;
-    return c;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kProbeItems / 2; ++k) {
+      const int loc = half * (kProbeTile / 2) + k * kThreads + tid;
+      const uint64_t row = base + loc;
+      if (row < np) __stcs(local + row, OffT(s_off[loc - half * (kProbeTile / 2)]));
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    tile_total[blockIdx.x] = tile_sum;
+    if (sizeof(OffT) < 8 && tile_sum > 0xffffffffull) atomicOr(status, 4u);  // needs 64-bit local offsets
+  }
+}
+
+// Exclusive scan of the count tiles' totals by one CTA: tile_base[t], and the
+// join's row count in tile_base[ntiles].
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const uint64_t* __restrict__ tile_total, uint64_t ntiles,
+                                                        uint64_t* __restrict__ tile_base) {
+  __shared__ uint64_t s_warp[32];
+  __shared__ uint64_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint64_t b = 0; b < ntiles; b += blockDim.x) {
+    const uint64_t i = b + threadIdx.x;
+    const uint64_t v = i < ntiles ? tile_total[i] : 0ull;
+    uint64_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint64_t x = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += x;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint64_t before = s_carry, chunk = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      if (w < warp) before += s_warp[w];
+      chunk += s_warp[w];
+    }
+    if (i < ntiles) tile_base[i] = before + inc - v;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += chunk;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tile_base[ntiles] = s_carry;
+}
+
+// Output offset of probe row i (i == np gives the row count).
+template <class OffT>
+struct Offsets {
+  const OffT* local;
+  const uint64_t* tile_base;
+  uint64_t np, T;
+  __device__ __forceinline__ uint64_t at(uint64_t i) const {
+    return i < np ? tile_base[i / kProbeTile] + uint64_t(local[i]) : T;
+  }
+  // the probe row whose output range holds output row v, searched in [lo, hi)
+  __device__ __forceinline__ uint64_t row_of(uint64_t v, uint64_t lo, uint64_t hi) const {
+    while (lo < hi) {
+      uint64_t mid = lo + (hi - lo) / 2;
+      if (at(mid) <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
   }
 };
 
-__global__ void __launch_bounds__(kLbThreads) probe_count_kernel(KeyCols pk, uint64_t np, const Slot* __restrict__ tab,
-                                                                 uint32_t M, uint32_t* __restrict__ pbeg,
-                                                                 uint64_t* __restrict__ off, uint64_t* scratch,
-                                                                 uint32_t* err) {
-  ProbeCounts pc{pk, tab, M, pbeg};
-  lookback_scan_tile<uint64_t>(pc, np, off, scratch, err);
+template <class T>
+__device__ __forceinline__ uint64_t upper_bound_t(const T* a, uint64_t lo, uint64_t hi, uint64_t v) {
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (uint64_t(a[mid]) <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
 }
 
+// Merge-path partition of the output: part[t] = the probe row whose output
+// range holds output row min(t * kWriteTile, T - 1), for t in [0, ntiles]:
+// first the count tile (search over tile bases), then the row inside it.
+template <class OffT>
+__global__ void write_partition_kernel(Offsets<OffT> off, uint64_t count_tiles, uint64_t ntiles,
+                                       uint64_t* __restrict__ part) {
+  for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t <= ntiles; t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t v = min(t * uint64_t(kWriteTile), off.T - 1);
+    const uint64_t ct = upper_bound_t(off.tile_base, 0, count_tiles + 1, v) - 1;
+    const uint64_t lo = ct * kProbeTile, hi = min(lo + kProbeTile, off.np);
+    part[t] = lo + upper_bound_t(off.local + lo, 0, hi - lo, v - off.tile_base[ct]) - 1;
+  }
+}
+
+template <class OffT>
 struct WriteParams {
-  const uint64_t* off;   // exclusive prefix sums of the probe counts (np + 1)
-  const uint32_t* pbeg;  // group start per probe row
+  Offsets<OffT> off;
+  const uint64_t* part;  // probe row of each output tile's first row (ntiles + 1)
+  const uint32_t* pbeg;  // group start of each probe row
   uint64_t np, nb, T;
   const uint32_t* src[MAPSQ_MAX_VARS];
   uint32_t* out[MAPSQ_MAX_VARS];
-  uint32_t from_build;   // bit c: column c comes from the grouped build side
+  uint32_t from_build;   // bit c: column c comes from the build side
+  uint32_t bstride;      // words between consecutive build rows in src (row-major grouped values)
   int ncols;
-  int cross;             // 1: cross product (no key), offsets implicit
 };
 
-__device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t* a, uint64_t lo, uint64_t hi, uint64_t v) {
+__device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t v) {
   while (lo < hi) {
-    uint64_t mid = lo + (hi - lo) / 2;
+    uint32_t mid = (lo + hi) >> 1;
     if (a[mid] <= v) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
-// Write pass: CTA tiles of kWriteTile output rows; each thread writes 4-row
-// groups of every output column with one 16-byte streaming store.
-__global__ void __launch_bounds__(kWriteThreads) join_write_kernel(WriteParams p) {
-  __shared__ uint64_t s_off[kOffCache + 1];
-  __shared__ uint64_t s_ilo, s_ihi;
+// Write pass: CTA tiles of kWriteTile output rows.  (1) The probe rows feeding
+// the tile get their output offsets (relative to the tile) and group starts
+// staged in shared memory.  (2) Every thread maps 16 consecutive output rows to
+// (probe row, build row) with one 32-bit search and a short walk, into shared
+// memory.  (3) Every thread takes 16 rows striped over the block (a row per
+// lane), reads their map entries once, and for every column issues the 16
+// gathers before the 16 coalesced streaming stores.
+template <class OffT>
+__global__ void __launch_bounds__(kThreads, 4) join_write_kernel(WriteParams<OffT> p) {
+  __shared__ uint32_t s_rel[kStageRows + 1];
+  __shared__ uint32_t s_beg[kStageRows];
+  __shared__ uint32_t s_pk[kMapWords];  // probe row of each output row (relative to the tile's first)
+  __shared__ uint32_t s_bk[kMapWords];  // build row of each output row
+  // row q lives at q + q / 32: conflict-free both for the 16 consecutive rows a
+  // thread maps and for the rows striped over the block that it gathers
+  auto mi = [](uint32_t q) { return q + (q >> 5); };
+  __shared__ uint32_t s_skip;
   const uint64_t ntiles = (p.T + kWriteTile - 1) / kWriteTile;
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const uint64_t t0 = tile * kWriteTile;
-    const uint64_t t1 = min(t0 + uint64_t(kWriteTile), p.T);
-    bool cached = false;
-    uint64_t ilo = 0, ihi = 0;
-    if (!p.cross) {
-      if (threadIdx.x == 0) {
-        // probe rows whose output range meets [t0, t1)
-        uint64_t a = upper_bound_u64(p.off, 0, p.np + 1, t0) - 1;
-        uint64_t b = upper_bound_u64(p.off, a, p.np + 1, t1 - 1) - 1;
-        s_ilo = a;
-        s_ihi = b;
+    const uint32_t n = uint32_t(min(uint64_t(kWriteTile), p.T - t0));
+    const uint64_t ilo = p.part[tile];
+    const uint64_t nst = p.part[tile + 1] - ilo + 1;  // probe rows ilo .. part[tile + 1] can feed this tile
+    const uint32_t q0 = threadIdx.x * kWriteRows;
+    if (nst <= kStageRows) {
+      const uint32_t ns = uint32_t(nst);
+      for (uint32_t k = threadIdx.x; k <= ns; k += kThreads) {
+        const uint64_t v = p.off.at(ilo + k);
+        s_rel[k] = v <= t0 ? 0u : uint32_t(min(v - t0, uint64_t(kWriteTile)));
       }
+      for (uint32_t k = threadIdx.x; k < ns; k += kThreads) s_beg[k] = p.pbeg[ilo + k];
+      if (threadIdx.x == 0) s_skip = uint32_t(t0 - p.off.at(ilo));  // rows of probe row ilo before this tile
       __syncthreads();
-      ilo = s_ilo;
-      ihi = s_ihi;
-      cached = ihi - ilo + 2 <= kOffCache + 1;
-      if (cached)
-        for (uint64_t k = threadIdx.x; k < ihi - ilo + 2; k += blockDim.x) s_off[k] = p.off[ilo + k];
-      __syncthreads();
-    }
-    for (int g = 0; g < kWriteGroups; ++g) {
-      const uint64_t r0 = t0 + 4ull * (threadIdx.x + uint64_t(g) * kWriteThreads);
-      if (r0 >= t1) break;
-      const int nr = int(min(uint64_t(4), t1 - r0));
-      uint64_t pi[4];
-      uint64_t bi[4];
-      if (p.cross) {
-        uint64_t i = r0 / p.nb, j = r0 - i * p.nb;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          pi[k] = i;
-          bi[k] = j;
-          if (++j == p.nb) { j = 0; ++i; }
-        }
-      } else {
-        uint64_t i;
-        if (cached) {
-          i = ilo + upper_bound_u64(s_off, 0, ihi - ilo + 2, r0) - 1;
-        } else {
-          i = upper_bound_u64(p.off, ilo, ihi + 2, r0) - 1;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint64_t r = r0 + k;
-          if (k < nr) {
-            // next probe row with a match: a binary search, since rows without
-            // matches can sit between two output rows
-            if (cached) {
-              if (s_off[i + 1 - ilo] <= r) i = ilo + upper_bound_u64(s_off, i + 1 - ilo, ihi - ilo + 2, r) - 1;
-              bi[k] = p.pbeg[i] + (r - s_off[i - ilo]);
-            } else {
-              if (p.off[i + 1] <= r) i = upper_bound_u64(p.off, i + 1, ihi + 2, r) - 1;
-              bi[k] = p.pbeg[i] + (r - p.off[i]);
-            }
-          } else {
-            bi[k] = 0;
+      if (q0 < n) {
+        uint32_t k = upper_bound_u32(s_rel, 0, ns + 1, q0) - 1;
+        const uint32_t skip = s_skip;
+#pragma unroll 4
+        for (int j = 0; j < kWriteRows; ++j) {
+          const uint32_t q = q0 + j;
+          if (q >= n) break;
+          if (s_rel[k + 1] <= q) {
+            ++k;
+            if (s_rel[k + 1] <= q) k = upper_bound_u32(s_rel, k + 1, ns + 1, q) - 1;
           }
-          pi[k] = i;
+          s_pk[mi(q)] = k;
+          s_bk[mi(q)] = s_beg[k] + (q - s_rel[k]) + (k == 0 ? skip : 0u);
         }
       }
-      for (int c = 0; c < p.ncols; ++c) {
-        const uint32_t* src = p.src[c];
-        const bool fb = (p.from_build >> c) & 1u;
-        uint32_t v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = k < nr ? __ldg(src + (fb ? bi[k] : pi[k])) : 0u;
-        uint32_t* dst = p.out[c] + r0;
-        if (nr == 4) {
-          __stcs(reinterpret_cast<uint4*>(dst), make_uint4(v[0], v[1], v[2], v[3]));
-        } else {
-          for (int k = 0; k < nr; ++k) __stcs(dst + k, v[k]);
-        }
+    } else if (q0 < n) {
+      // more probe rows than the stage holds (rows with few matches): global search
+      const uint64_t hi = ilo + nst + 1;
+      uint64_t i = p.off.row_of(t0 + q0, ilo, hi);
+      for (int j = 0; j < kWriteRows; ++j) {
+        const uint32_t q = q0 + j;
+        if (q >= n) break;
+        const uint64_t r = t0 + q;
+        if (p.off.at(i + 1) <= r) i = p.off.row_of(r, i + 1, hi);
+        s_pk[mi(q)] = uint32_t(i - ilo);
+        s_bk[mi(q)] = p.pbeg[i] + uint32_t(r - p.off.at(i));
       }
     }
     __syncthreads();
+    uint32_t pk[kWriteRows], bk[kWriteRows];
+#pragma unroll
+    for (int j = 0; j < kWriteRows; ++j) {
+      const uint32_t q = uint32_t(j) * kThreads + threadIdx.x;
+      pk[j] = q < n ? s_pk[mi(q)] : 0u;
+      bk[j] = q < n ? s_bk[mi(q)] : 0u;
+    }
+    for (int c = 0; c < p.ncols; ++c) {
+      const bool fb = (p.from_build >> c) & 1u;
+      const uint32_t* src = fb ? p.src[c] : p.src[c] + ilo;
+      const uint32_t st = fb ? p.bstride : 1u;
+      uint32_t* dst = p.out[c] + t0;
+      uint32_t x[kWriteRows];
+#pragma unroll
+      for (int j = 0; j < kWriteRows; ++j) {
+        const uint32_t q = uint32_t(j) * kThreads + threadIdx.x;
+        x[j] = q < n ? __ldg(src + uint64_t(fb ? bk[j] : pk[j]) * st) : 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < kWriteRows; ++j) {
+        const uint32_t q = uint32_t(j) * kThreads + threadIdx.x;
+        if (q < n) __stcs(dst + q, x[j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+struct CrossParams {
+  uint64_t np, nb, T;
+  const uint32_t* src[MAPSQ_MAX_VARS];
+  uint32_t* out[MAPSQ_MAX_VARS];
+  uint32_t from_build;   // bit c: column c comes from the smaller table
+  int ncols;
+};
+
+// Cross product (no shared variable): output row r pairs probe row r / nb with
+// build row r % nb.
+__global__ void __launch_bounds__(kThreads) cross_write_kernel(CrossParams p) {
+  const uint64_t ngroups = (p.T + 3) / 4;
+  for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t r0 = 4 * g;
+    const int nr = int(min(uint64_t(4), p.T - r0));
+    uint64_t pi[4], bi[4];
+    uint64_t i = r0 / p.nb, j = r0 - i * p.nb;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pi[k] = i;
+      bi[k] = j;
+      if (++j == p.nb) { j = 0; ++i; }
+    }
+    for (int c = 0; c < p.ncols; ++c) {
+      const bool fb = (p.from_build >> c) & 1u;
+      uint32_t v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = k < nr ? __ldg(p.src[c] + (fb ? bi[k] : pi[k])) : 0u;
+      if (nr == 4) {
+        __stcs(reinterpret_cast<uint4*>(p.out[c] + r0), make_uint4(v[0], v[1], v[2], v[3]));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < nr) __stcs(p.out[c] + r0 + k, v[k]);
+      }
+    }
   }
 }
 
@@ -352,136 +667,274 @@ int check_table(Ctx* ctx, const mapsq_table* t, const char* which) {
   return MAPSQ_OK;
 }
 
-}  // namespace
-
-int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
-                TableImpl** out) {
-  (void)opts;
-  MQ_TRY(check_table(ctx, L, "left"));
-  MQ_TRY(check_table(ctx, R, "right"));
+// One join, split in two halves so that the caller can allocate the output once
+// its size is known: count() runs the map, shuffle and count passes and sets T;
+// write() runs the partition and write passes.  Device memory comes from
+// ``Mem`` (the context's allocator, or a fixed array carved by the caller), and
+// ``host`` is a host buffer of at least kHllRegs / 2 + 2 words for read-backs.
+template <class Mem>
+struct HashJoin {
+  Ctx* ctx;               // NULL without a context (no profiling, no launch count)
+  cudaStream_t stream;
+  uint32_t* status;       // device status word
+  Mem* mem;
+  uint64_t* host;
   Layout lay;
-  MQ_TRY(make_layout(ctx, L, R, &lay));
-  // build on the smaller side, probe with the larger
-  const bool build_left = L->nrows < R->nrows;
-  const mapsq_table* B = build_left ? L : R;
-  const mapsq_table* P = build_left ? R : L;
-  const int bside = build_left ? 0 : 1;
-  const int* bkey = build_left ? lay.lkey : lay.rkey;
-  const int* pkey = build_left ? lay.rkey : lay.lkey;
-  const uint64_t nb = B->nrows, np = P->nrows;
+  const mapsq_table *L = nullptr, *R = nullptr, *B = nullptr, *P = nullptr;
+  int bside = 1;
+  const int *bkey = nullptr, *pkey = nullptr;
+  uint64_t nb = 0, np = 0, T = 0;
+  bool cross = false, off32 = true;
+  KeyCols bk{}, pk{};
+  HashTable table{};
+  uint64_t M = 0;
+  uint32_t* grouped = nullptr;
+  uint32_t nbv = 0;       // build value columns (row-major stride of ``grouped``)
+  uint64_t nt = 0;                 // count tiles
+  void* local = nullptr;           // tile-local output offsets of the probe rows (u32 or u64)
+  uint32_t* pbeg = nullptr;        // group start of each probe row
+  uint64_t* tile_base = nullptr;   // nt + 1
 
-  if (nb >= (uint64_t(1) << 31))
-    return set_error(ctx, MAPSQ_ERR_UNSUPPORTED, "build side of %llu rows (at most 2^31-1)", (unsigned long long)nb);
-
-  Scratch scratch(ctx);
-  uint64_t T = 0;
-  uint64_t* off = nullptr;
-  uint32_t* pbeg = nullptr;
-  uint32_t* grouped[MAPSQ_MAX_VARS] = {};
-  const bool cross = lay.nkey == 0;
-
-  if (nb == 0 || np == 0) {
-    T = 0;
-  } else if (cross) {
-    if (np > UINT64_MAX / nb) return set_error(ctx, MAPSQ_ERR_BUDGET, "cross product overflows 64 bits");
-    T = np * nb;
-  } else {
-    KeyCols bk{B->col[bkey[0]], lay.nkey == 2 ? B->col[bkey[1]] : nullptr};
-    KeyCols pk{P->col[pkey[0]], lay.nkey == 2 ? P->col[pkey[1]] : nullptr};
-    uint64_t M = std::max<uint64_t>(1024, 2 * nb);
-    if (M >= 0xffffffffull) M = 0xfffffffeull;
-    Slot* tab = nullptr;
-    uint32_t *cnt = nullptr, *beg = nullptr, *slot_of = nullptr, *rank_of = nullptr;
-    MQ_TRY(scratch.get(M + 1, &tab));
-    MQ_TRY(scratch.get(M + 2, &cnt));
-    MQ_TRY(scratch.get(M + 2, &beg));
-    MQ_TRY(scratch.get(nb, &slot_of));
-    MQ_TRY(scratch.get(nb, &rank_of));
-    hash_init_kernel<<<grid_for(M + 1, 152ull * 32), 256, 0, ctx->stream>>>(tab, cnt, M + 1);
-    ++ctx->launches;
-    int rec = prof_begin(ctx, K_HASH_INSERT);
-    hash_insert_kernel<<<grid_for(nb, 152ull * 32), 256, 0, ctx->stream>>>(bk, nb, tab, cnt, uint32_t(M), slot_of,
-                                                                            rank_of, ctx->d_status);
-    ++ctx->launches;
-    prof_end(ctx, rec, 4.0 * lay.nkey * nb);
-    MQ_CUDA(cudaGetLastError());
-    MQ_TRY(prefix_sum_u32_u32(ctx, cnt, beg, M + 1));
-    hash_finalize_kernel<<<grid_for(M + 1, 152ull * 32), 256, 0, ctx->stream>>>(tab, cnt, beg, M + 1);
-    ++ctx->launches;
-    // group the build side's value columns
-    ValueCols vc{};
-    for (int c = 0; c < lay.ncols; ++c) {
-      if (lay.side[c] != bside) continue;
-      MQ_TRY(scratch.get(nb, &grouped[c]));
-      vc.src[vc.n] = B->col[lay.col[c]];
-      vc.dst[vc.n] = grouped[c];
-      ++vc.n;
-    }
-    if (vc.n) {
-      rec = prof_begin(ctx, K_HASH_SCATTER);
-      hash_scatter_kernel<<<grid_for(nb, 152ull * 32), 256, 0, ctx->stream>>>(vc, nb, slot_of, rank_of, beg);
-      ++ctx->launches;
-      prof_end(ctx, rec, 4.0 * vc.n * nb);
-      MQ_CUDA(cudaGetLastError());
-    }
-    // count pass fused with the prefix sum of the counts
-    uint64_t* lb = nullptr;
-    MQ_TRY(scratch.get(np, &pbeg));
-    MQ_TRY(scratch.get(np + 1, &off));
-    MQ_TRY(scratch.get(lookback_scratch_words(np), &lb));
-    MQ_CUDA(cudaMemsetAsync(lb, 0, lookback_scratch_words(np) * sizeof(uint64_t), ctx->stream));
-    rec = prof_begin(ctx, K_PROBE_COUNT);
-    probe_count_kernel<<<unsigned(ceil_div(np, kLbTile)), kLbThreads, 0, ctx->stream>>>(pk, np, tab, uint32_t(M), pbeg,
-                                                                                        off, lb, ctx->d_status);
-    ++ctx->launches;
-    prof_end(ctx, rec, 4.0 * lay.nkey * np);
-    MQ_CUDA(cudaGetLastError());
-    // also reports a full hash table (impossible with M >= 2 nb) through the status word
-    MQ_TRY(read_u64(ctx, off + np, &T, 1));
+  int fail(int code, const char* what) { return ctx ? set_error(ctx, code, "%s", what) : code; }
+  int cuda(cudaError_t e, const char* what) {
+    return e == cudaSuccess ? MAPSQ_OK : (ctx ? cuda_fail(ctx, e, what, __FILE__, __LINE__) : MAPSQ_ERR_CUDA);
+  }
+  void launched() {
+    if (ctx) ++ctx->launches;
+  }
+  int rec(int kid) { return ctx ? prof_begin(ctx, kid) : -1; }
+  void done(int r, double bytes) {
+    if (ctx) prof_end(ctx, r, bytes);
   }
 
-  TableImpl* t = nullptr;
-  if (lay.ncols == 0) {
-    MQ_TRY(table_alloc(ctx, T, 0, lay.var, &t));
-    *out = t;
+  int prepare(const mapsq_table* left, const mapsq_table* right) {
+    L = left;
+    R = right;
+    MQ_TRY(check_table(ctx, L, "left"));
+    MQ_TRY(check_table(ctx, R, "right"));
+    MQ_TRY(make_layout(ctx, L, R, &lay));
+    const bool build_left = L->nrows < R->nrows;  // build on the smaller side
+    B = build_left ? L : R;
+    P = build_left ? R : L;
+    bside = build_left ? 0 : 1;
+    bkey = build_left ? lay.lkey : lay.rkey;
+    pkey = build_left ? lay.rkey : lay.lkey;
+    nb = B->nrows;
+    np = P->nrows;
+    cross = lay.nkey == 0;
+    if (nb >= (uint64_t(1) << 31)) return fail(MAPSQ_ERR_UNSUPPORTED, "build side of 2^31 rows or more");
+    if (!cross) {
+      bk = KeyCols{B->col[bkey[0]], lay.nkey == 2 ? B->col[bkey[1]] : nullptr};
+      pk = KeyCols{P->col[pkey[0]], lay.nkey == 2 ? P->col[pkey[1]] : nullptr};
+    }
     return MAPSQ_OK;
   }
-  MQ_TRY(table_alloc(ctx, T, uint32_t(lay.ncols), lay.var, &t));
-  if (T) {
-    WriteParams wp{};
-    wp.off = off;
+
+  // Reads ``count`` 64-bit words and then the status word, synchronising the stream.
+  int readback(const void* dptr, int count) {
+    host[count] = 0;  // the status word fills only its low half
+    MQ_TRY(cuda(cudaMemcpyAsync(host, dptr, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost, stream), "readback"));
+    MQ_TRY(cuda(cudaMemcpyAsync(host + count, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream), "status"));
+    MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
+    return MAPSQ_OK;
+  }
+
+  int build_table() {
+    uint32_t *slot_of = nullptr, *rank_of = nullptr;
+    uint64_t* lb = nullptr;
+    MQ_TRY(mem->get(M, &table.keys));
+    MQ_TRY(mem->get(M + 1, &table.group));
+    table.M = uint32_t(M);
+    MQ_TRY(mem->get(nb, &slot_of));
+    MQ_TRY(mem->get(nb, &rank_of));
+    MQ_TRY(mem->get(lookback_scratch_words(M + 1), &lb));
+    MQ_TRY(cuda(cudaMemsetAsync(lb, 0, lookback_scratch_words(M + 1) * sizeof(uint64_t), stream), "memset"));
+    MQ_TRY(cuda(cudaMemsetAsync(table.keys, 0xff, M * sizeof(uint64_t), stream), "memset"));  // all empty
+    MQ_TRY(cuda(cudaMemsetAsync(table.group, 0, (M + 1) * sizeof(uint2), stream), "memset"));
+    int r = rec(K_HASH_INSERT);
+    hash_insert_kernel<<<grid_for(nb, 152ull * 32), 256, 0, stream>>>(bk, nb, table, slot_of, rank_of, status);
+    launched();
+    done(r, 4.0 * lay.nkey * nb);
+    r = rec(K_PREFIX_SUM);
+    slot_prefix_kernel<<<unsigned(ceil_div(M + 1, kLbTile)), kLbThreads, 0, stream>>>(table.group, M + 1, lb, status);
+    launched();
+    done(r, 8.0 * (M + 1));
+    BuildValues bv{};
+    for (int c = lay.nkey; c < lay.ncols; ++c)
+      if (lay.side[c] == bside) bv.src[bv.n++] = B->col[lay.col[c]];
+    nbv = uint32_t(bv.n);
+    if (nbv) {
+      MQ_TRY(mem->get(nb * nbv, &grouped));
+      r = rec(K_HASH_SCATTER);
+      hash_scatter_kernel<<<grid_for(ceil_div(nb, kScatterRows), 152ull * 16), 256, 0, stream>>>(
+          bv, nb, slot_of, rank_of, table.group, grouped);
+      launched();
+      done(r, 4.0 * nbv * nb);
+    }
+    return cuda(cudaGetLastError(), "hash build kernels");
+  }
+
+  template <class OffT>
+  int probe() {
+    OffT* loc = nullptr;
+    uint64_t* tot = nullptr;
+    nt = ceil_div(np, kProbeTile);
+    MQ_TRY(mem->get(np, &loc));
+    if (!pbeg) MQ_TRY(mem->get(np, &pbeg));
+    MQ_TRY(mem->get(nt, &tot));
+    MQ_TRY(mem->get(nt + 1, &tile_base));
+    int r = rec(K_PROBE_COUNT);
+    probe_count_kernel<OffT><<<unsigned(nt), kThreads, 0, stream>>>(pk, np, table, loc, pbeg, tot, status);
+    launched();
+    done(r, 4.0 * lay.nkey * np);
+    tile_scan_kernel<<<1, 1024, 0, stream>>>(tot, nt, tile_base);
+    launched();
+    local = loc;
+    return cuda(cudaGetLastError(), "probe_count_kernel");
+  }
+
+  int count() {
+    T = 0;
+    if (nb == 0 || np == 0) return MAPSQ_OK;
+    if (cross) {
+      if (np > UINT64_MAX / nb) return fail(MAPSQ_ERR_BUDGET, "cross product overflows 64 bits");
+      T = np * nb;
+      return MAPSQ_OK;
+    }
+    MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
+    M = std::max<uint64_t>(1024, 2 * nb);
+    if (nb >= kHllMinBuild) {
+      // size the table from the distinct keys: load factor about 0.6
+      uint32_t* regs = nullptr;
+      MQ_TRY(mem->get(kHllRegs, &regs));
+      MQ_TRY(cuda(cudaMemsetAsync(regs, 0, kHllRegs * sizeof(uint32_t), stream), "memset"));
+      int r = rec(K_HLL);
+      hll_kernel<<<grid_for(nb / 4, 152ull * 8), 256, 0, stream>>>(bk, nb, regs);
+      launched();
+      done(r, 4.0 * lay.nkey * nb);
+      MQ_TRY(readback(regs, kHllRegs / 2));
+      double est = hll_estimate(reinterpret_cast<const uint32_t*>(host));
+      M = std::min<uint64_t>(M, std::max<uint64_t>(1024, uint64_t(1.6 * est) + 1024));
+    }
+    if (M >= 0xfffffff0ull) M = 0xfffffff0ull;
+    M = (M + kBucket - 1) / kBucket * kBucket;
+    for (int attempt = 0;; ++attempt) {
+      MQ_TRY(build_table());
+      if (off32) {
+        MQ_TRY(probe<uint32_t>());
+      } else {
+        MQ_TRY(probe<uint64_t>());
+      }
+      MQ_TRY(readback(tile_base + nt, 1));
+      const uint32_t st = uint32_t(host[1]);
+      if (st & 1u) {
+        // a distinct-key estimate far too low: rebuild at two slots per build row
+        if (attempt > 0 || M >= 2 * nb) return fail(MAPSQ_ERR_CUDA, "hash table full");
+        M = (std::max<uint64_t>(1024, 2 * nb) + kBucket - 1) / kBucket * kBucket;
+        MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
+        continue;
+      }
+      if (st & 2u) return fail(MAPSQ_ERR_TIMEOUT, "a prefix-sum look-back wait gave up");
+      if (st & 4u) {
+        // a count tile's total needs 64-bit local offsets: count again with them
+        if (!off32) return fail(MAPSQ_ERR_CUDA, "device status word set");
+        off32 = false;
+        MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
+        MQ_TRY(probe<uint64_t>());
+        MQ_TRY(readback(tile_base + nt, 1));
+        if (host[1]) return fail(MAPSQ_ERR_CUDA, "device status word set");
+      } else if (st) {
+        return fail(MAPSQ_ERR_CUDA, "device status word set");
+      }
+      T = host[0];
+      return MAPSQ_OK;
+    }
+  }
+
+  template <class OffT>
+  int write_hash(uint32_t* const* out_cols) {
+    WriteParams<OffT> wp{};
+    wp.off = Offsets<OffT>{static_cast<const OffT*>(local), tile_base, np, T};
     wp.pbeg = pbeg;
     wp.np = np;
     wp.nb = nb;
     wp.T = T;
     wp.ncols = lay.ncols;
-    wp.cross = cross ? 1 : 0;
+    wp.bstride = nbv;
+    const uint64_t ntiles = ceil_div(T, kWriteTile);
+    uint64_t* part = nullptr;
+    MQ_TRY(mem->get(ntiles + 1, &part));
+    int r = rec(K_PARTITION);
+    write_partition_kernel<OffT><<<grid_for(ntiles + 1, 152ull * 8), 256, 0, stream>>>(wp.off, nt, ntiles, part);
+    launched();
+    done(r, 8.0 * (ntiles + 1));
+    wp.part = part;
     double in_bytes = 0;
+    uint32_t j = 0;
     for (int c = 0; c < lay.ncols; ++c) {
       const bool fb = lay.side[c] == bside && c >= lay.nkey;
-      wp.out[c] = t->pub.col[c];
+      wp.out[c] = out_cols[c];
       if (fb) {
-        wp.src[c] = cross ? B->col[lay.col[c]] : grouped[c];
+        wp.src[c] = grouped + j++;
         wp.from_build |= 1u << c;
         in_bytes += 4.0 * nb;
       } else {
         // key columns and the probe side's own columns come from the probe row
-        int pc = c < lay.nkey ? pkey[c] : lay.col[c];
-        wp.src[c] = P->col[pc];
+        wp.src[c] = P->col[c < lay.nkey ? pkey[c] : lay.col[c]];
         if (c >= lay.nkey) in_bytes += 4.0 * np;
       }
     }
-    uint64_t ntiles = ceil_div(T, kWriteTile);
     unsigned grid = unsigned(std::min<uint64_t>(ntiles, 152ull * 8));
-    int rec = prof_begin(ctx, cross ? K_CROSS_WRITE : K_JOIN_WRITE);
-    join_write_kernel<<<grid, kWriteThreads, 0, ctx->stream>>>(wp);
-    ++ctx->launches;
-    prof_end(ctx, rec, 4.0 * double(T) * lay.ncols + in_bytes);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      table_release(ctx, t);
-      return cuda_fail(ctx, e, "join_write_kernel", __FILE__, __LINE__);
+    r = rec(K_JOIN_WRITE);
+    join_write_kernel<OffT><<<grid, kThreads, 0, stream>>>(wp);
+    launched();
+    done(r, 4.0 * double(T) * lay.ncols + in_bytes);
+    return cuda(cudaGetLastError(), "join_write_kernel");
+  }
+
+  int write_cross(uint32_t* const* out_cols) {
+    CrossParams cp{};
+    cp.np = np;
+    cp.nb = nb;
+    cp.T = T;
+    cp.ncols = lay.ncols;
+    double in_bytes = 0;
+    for (int c = 0; c < lay.ncols; ++c) {
+      const bool fb = lay.side[c] == bside;
+      cp.out[c] = out_cols[c];
+      cp.src[c] = (fb ? B : P)->col[lay.col[c]];
+      if (fb) cp.from_build |= 1u << c;
+      in_bytes += 4.0 * (fb ? nb : np);
     }
+    int r = rec(K_CROSS_WRITE);
+    cross_write_kernel<<<grid_for(ceil_div(T, 4), 152ull * 8), kThreads, 0, stream>>>(cp);
+    launched();
+    done(r, 4.0 * double(T) * lay.ncols + in_bytes);
+    return cuda(cudaGetLastError(), "cross_write_kernel");
+  }
+
+  int write(uint32_t* const* out_cols) {
+    if (T == 0 || lay.ncols == 0) return MAPSQ_OK;
+    if (cross) return write_cross(out_cols);
+    return off32 ? write_hash<uint32_t>(out_cols) : write_hash<uint64_t>(out_cols);
+  }
+};
+
+}  // namespace
+
+int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
+                TableImpl** out) {
+  (void)opts;
+  Scratch scratch(ctx);
+  HashJoin<Scratch> j{ctx, ctx->stream, ctx->d_status, &scratch, ctx->h_pinned + 64};
+  MQ_TRY(j.prepare(L, R));
+  MQ_TRY(j.count());
+  TableImpl* t = nullptr;
+  MQ_TRY(table_alloc(ctx, j.T, uint32_t(j.lay.ncols), j.lay.var, &t));
+  int rc = j.write(t->pub.col);
+  if (rc != MAPSQ_OK) {
+    table_release(ctx, t);
+    return rc;
   }
   *out = t;
   return MAPSQ_OK;
@@ -526,28 +979,18 @@ int noalloc_scratch(unsigned char** out) {
   return MAPSQ_OK;
 }
 
-struct SlotCounts {
-  const uint32_t* cnt;
-  __device__ __forceinline__ uint32_t operator()(uint64_t i) const { return cnt[i]; }
-};
-
-// Prefix sum of the hash slots' group sizes (group starts), scratch passed in.
-__global__ void __launch_bounds__(kLbThreads) noalloc_slot_prefix_kernel(const uint32_t* __restrict__ cnt, uint64_t n,
-                                                                         uint32_t* __restrict__ beg, uint64_t* lb,
-                                                                         uint32_t* err) {
-  SlotCounts v{cnt};
-  lookback_scan_tile<uint32_t>(v, n, beg, lb, err);
-}
-
-// Bump carving of the scratch array, 256-byte aligned regions.
+// Bump carving of the scratch array into 256-byte aligned regions; refuses to
+// run past its end.
 struct Carve {
   unsigned char* base;
   size_t used = 0;
   template <class T>
-  T* take(uint64_t count) {
-    T* p = reinterpret_cast<T*>(base + used);
-    used += (size_t(count) * sizeof(T) + 255) & ~size_t(255);
-    return p;
+  int get(size_t count, T** out) {
+    size_t bytes = (std::max<size_t>(count * sizeof(T), 16) + 255) & ~size_t(255);
+    if (used + bytes > kNoAllocScratchBytes) return MAPSQ_ERR_INVALID;
+    *out = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return MAPSQ_OK;
   }
 };
 
@@ -561,112 +1004,27 @@ extern "C" int mapsq_join_noalloc(const mapsq_table* left, const mapsq_table* ri
                                   uint64_t out_capacity_rows, mapsq_table* out, uint64_t* out_rows,
                                   void* cuda_stream) {
   if (!left || !right || !out || !out_rows) return MAPSQ_ERR_INVALID;
-  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  MQ_TRY(check_table(nullptr, left, "left"));
-  MQ_TRY(check_table(nullptr, right, "right"));
-  Layout lay;
-  MQ_TRY(make_layout(nullptr, left, right, &lay));
-  const bool build_left = left->nrows < right->nrows;
-  const mapsq_table* B = build_left ? left : right;
-  const mapsq_table* P = build_left ? right : left;
-  const int bside = build_left ? 0 : 1;
-  const int* bkey = build_left ? lay.lkey : lay.rkey;
-  const int* pkey = build_left ? lay.rkey : lay.lkey;
-  const uint64_t nb = B->nrows, np = P->nrows;
-  if (nb > kNoAllocMaxBuild || np > kNoAllocMaxProbe) return MAPSQ_ERR_INVALID;  // beyond the scratch array
-  if (lay.ncols && !out_cols) return MAPSQ_ERR_INVALID;
-  for (int c = 0; c < lay.ncols; ++c)
-    if (!out_cols[c] || (reinterpret_cast<uintptr_t>(out_cols[c]) & 15)) return MAPSQ_ERR_INVALID;
-
   unsigned char* base = nullptr;
   MQ_TRY(noalloc_scratch(&base));
-  Carve cv{base};
-  uint32_t* status = cv.take<uint32_t>(64);
-  const bool cross = lay.nkey == 0;
-  uint64_t T = 0;
-  uint64_t* off = nullptr;
-  uint32_t* pbeg = nullptr;
-  uint32_t* grouped[MAPSQ_MAX_VARS] = {};
-  if (nb == 0 || np == 0) {
-    T = 0;
-  } else if (cross) {
-    T = np * nb;  // both below 2^20: no overflow
-  } else {
-    KeyCols bk{B->col[bkey[0]], lay.nkey == 2 ? B->col[bkey[1]] : nullptr};
-    KeyCols pk{P->col[pkey[0]], lay.nkey == 2 ? P->col[pkey[1]] : nullptr};
-    const uint64_t M = std::max<uint64_t>(1024, 2 * nb);
-    Slot* tab = cv.take<Slot>(M + 1);
-    uint32_t* cnt = cv.take<uint32_t>(M + 2);
-    uint32_t* beg = cv.take<uint32_t>(M + 2);
-    uint32_t* slot_of = cv.take<uint32_t>(nb);
-    uint32_t* rank_of = cv.take<uint32_t>(nb);
-    ValueCols vc{};
-    for (int c = 0; c < lay.ncols; ++c) {
-      if (lay.side[c] != bside) continue;
-      grouped[c] = cv.take<uint32_t>(nb);
-      vc.src[vc.n] = B->col[lay.col[c]];
-      vc.dst[vc.n] = grouped[c];
-      ++vc.n;
-    }
-    pbeg = cv.take<uint32_t>(np);
-    off = cv.take<uint64_t>(np + 1);
-    uint64_t* lb_slots = cv.take<uint64_t>(lookback_scratch_words(M + 1));
-    uint64_t* lb_probe = cv.take<uint64_t>(lookback_scratch_words(np));
-    if (cv.used > kNoAllocScratchBytes) return MAPSQ_ERR_INVALID;
-    // every call starts from cleared state: the array keeps the previous call's contents
-    if (cudaMemsetAsync(status, 0, 64 * sizeof(uint32_t), stream) != cudaSuccess ||
-        cudaMemsetAsync(lb_slots, 0, lookback_scratch_words(M + 1) * sizeof(uint64_t), stream) != cudaSuccess ||
-        cudaMemsetAsync(lb_probe, 0, lookback_scratch_words(np) * sizeof(uint64_t), stream) != cudaSuccess)
-      return MAPSQ_ERR_CUDA;
-    hash_init_kernel<<<grid_for(M + 1, 152ull * 32), 256, 0, stream>>>(tab, cnt, M + 1);
-    hash_insert_kernel<<<grid_for(nb, 152ull * 32), 256, 0, stream>>>(bk, nb, tab, cnt, uint32_t(M), slot_of, rank_of,
-                                                                      status);
-    noalloc_slot_prefix_kernel<<<unsigned(ceil_div(M + 1, kLbTile)), kLbThreads, 0, stream>>>(cnt, M + 1, beg,
-                                                                                              lb_slots, status);
-    hash_finalize_kernel<<<grid_for(M + 1, 152ull * 32), 256, 0, stream>>>(tab, cnt, beg, M + 1);
-    if (vc.n) hash_scatter_kernel<<<grid_for(nb, 152ull * 32), 256, 0, stream>>>(vc, nb, slot_of, rank_of, beg);
-    probe_count_kernel<<<unsigned(ceil_div(np, kLbTile)), kLbThreads, 0, stream>>>(pk, np, tab, uint32_t(M), pbeg, off,
-                                                                                   lb_probe, status);
-    if (cudaGetLastError() != cudaSuccess) return MAPSQ_ERR_CUDA;
-    uint64_t host[2] = {0, 0};
-    if (cudaMemcpyAsync(&host[0], off + np, sizeof(uint64_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaMemcpyAsync(&host[1], status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
-      return MAPSQ_ERR_CUDA;
-    if (host[1] & 2u) return MAPSQ_ERR_TIMEOUT;
-    if (host[1]) return MAPSQ_ERR_CUDA;
-    T = host[0];
-  }
-  *out_rows = T;
-  if (T > out_capacity_rows) return MAPSQ_ERR_BUDGET;
+  Carve carve{base};
+  uint32_t* status = nullptr;
+  MQ_TRY(carve.get(64, &status));
+  uint64_t host[kHllRegs / 2 + 8];
+  HashJoin<Carve> j{nullptr, static_cast<cudaStream_t>(cuda_stream), status, &carve, host};
+  MQ_TRY(j.prepare(left, right));
+  if (j.nb > kNoAllocMaxBuild || j.np > kNoAllocMaxProbe) return MAPSQ_ERR_INVALID;  // beyond the scratch array
+  const int ncols = j.lay.ncols;
+  if (ncols && !out_cols) return MAPSQ_ERR_INVALID;
+  for (int c = 0; c < ncols; ++c)
+    if (!out_cols[c] || (reinterpret_cast<uintptr_t>(out_cols[c]) & 15)) return MAPSQ_ERR_INVALID;
+  MQ_TRY(j.count());
+  *out_rows = j.T;
+  if (j.T > out_capacity_rows) return MAPSQ_ERR_BUDGET;
   memset(out, 0, sizeof(*out));
-  out->nrows = T;
-  out->ncols = uint32_t(lay.ncols);
+  out->nrows = j.T;
+  out->ncols = uint32_t(ncols);
   out->on_device = 1;
-  for (int c = 0; c < MAPSQ_MAX_VARS; ++c) out->var[c] = c < lay.ncols ? lay.var[c] : -1;
-  for (int c = 0; c < lay.ncols; ++c) out->col[c] = out_cols[c];
-  if (T && lay.ncols) {
-    WriteParams wp{};
-    wp.off = off;
-    wp.pbeg = pbeg;
-    wp.np = np;
-    wp.nb = nb;
-    wp.T = T;
-    wp.ncols = lay.ncols;
-    wp.cross = cross ? 1 : 0;
-    for (int c = 0; c < lay.ncols; ++c) {
-      const bool fb = lay.side[c] == bside && c >= lay.nkey;
-      wp.out[c] = out_cols[c];
-      if (fb) {
-        wp.src[c] = cross ? B->col[lay.col[c]] : grouped[c];
-        wp.from_build |= 1u << c;
-      } else {
-        wp.src[c] = P->col[c < lay.nkey ? pkey[c] : lay.col[c]];
-      }
-    }
-    unsigned grid = unsigned(std::min<uint64_t>(ceil_div(T, kWriteTile), 152ull * 8));
-    join_write_kernel<<<grid, kWriteThreads, 0, stream>>>(wp);
-    if (cudaGetLastError() != cudaSuccess) return MAPSQ_ERR_CUDA;
-  }
-  return MAPSQ_OK;
+  for (int c = 0; c < MAPSQ_MAX_VARS; ++c) out->var[c] = c < ncols ? j.lay.var[c] : -1;
+  for (int c = 0; c < ncols; ++c) out->col[c] = out_cols[c];
+  return j.write(out_cols);
 }

@@ -71,30 +71,37 @@ __device__ __forceinline__ uint64_t lb_tile_prefix(uint64_t* tile_status, uint32
   return prefix;
 }
 
-// One tile of the scan.  ``value(row)`` returns the uint32 value of a row
-// (< n) and may record side results; ``out`` receives n + 1 prefix sums.
-// ``scratch`` = [ticket, status[ntiles]] zeroed before the launch.
-template <class OutT, class Producer>
-__device__ __forceinline__ void lookback_scan_tile(Producer& value, uint64_t n, OutT* __restrict__ out,
-                                                   uint64_t* scratch, uint32_t* err) {
-  __shared__ uint64_t s_val[kLbTile + kLbTile / 16];
-  __shared__ uint32_t s_tile;
-  __shared__ uint64_t s_warp[kLbThreads / 32];
-  __shared__ uint64_t s_prefix;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = uint32_t(atomicAdd(reinterpret_cast<unsigned long long*>(&scratch[0]), 1ull));
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint64_t base = uint64_t(tile) * kLbTile;
-  // produce the tile's values in row order (coalesced, striped over threads)
+// A producer fills the tile's values in row order: ``fill(base, n, s)`` writes
+// s[lb_pad(k)] = value of row base + k for k in [0, kLbTile), 0 past row n.
+// Values are below 2^32.  Rows are striped over the threads for coalescing.
+struct LbArrayProducer {
+  const uint32_t* in;
+  __device__ __forceinline__ void fill(uint64_t base, uint64_t n, uint64_t* s) const {
 #pragma unroll 4
-  for (int k = 0; k < kLbItems; ++k) {
-    const int local = k * kLbThreads + tid;
-    const uint64_t row = base + local;
-    s_val[lb_pad(local)] = row < n ? uint64_t(value(row)) : 0ull;
+    for (int k = 0; k < kLbItems; ++k) {
+      const int local = k * kLbThreads + threadIdx.x;
+      const uint64_t row = base + local;
+      s[lb_pad(local)] = row < n ? uint64_t(in[row]) : 0ull;
+    }
   }
-  __syncthreads();
-  // each thread sums its 16 consecutive rows
+};
+
+// A sink receives the exclusive prefix sum of every row (``store``) and the
+// total (``total``, called once).
+template <class OutT>
+struct LbArraySink {
+  OutT* out;  // n + 1 entries: prefix sums, then the total
+  uint64_t n;
+  __device__ __forceinline__ void store(uint64_t row, uint64_t v) const { out[row] = OutT(v); }
+  __device__ __forceinline__ void total(uint64_t v) const { out[n] = OutT(v); }
+};
+
+// Block-wide exclusive scan of the tile held in ``s_val`` (kLbTile values in
+// row order, padded by lb_pad): each thread scans 16 consecutive values, the
+// threads' sums are scanned with warp shuffles.  Returns this thread's
+// exclusive prefix (within the tile) in *thread_excl and the tile's sum.
+__device__ __forceinline__ uint64_t lb_block_scan(const uint64_t* s_val, uint64_t* s_warp, uint64_t* thread_excl) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t sum = 0;
 #pragma unroll
   for (int k = 0; k < kLbItems; ++k) sum += s_val[lb_pad(tid * kLbItems + k)];
@@ -113,12 +120,35 @@ __device__ __forceinline__ void lookback_scan_tile(Producer& value, uint64_t n, 
     if (w < warp) warp_excl += x;
     tile_sum += x;
   }
+  *thread_excl = warp_excl + inc - sum;
+  return tile_sum;
+}
+
+// One tile of the scan over n values: ``sink`` receives every row's exclusive
+// prefix sum and the total.  ``scratch`` = [ticket, status[ntiles]], zeroed
+// before the launch.
+template <class Producer, class Sink>
+__device__ __forceinline__ void lookback_scan_tile(const Producer& prod, uint64_t n, const Sink& sink,
+                                                   uint64_t* scratch, uint32_t* err) {
+  __shared__ uint64_t s_val[kLbTile + kLbTile / 16];
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_warp[kLbThreads / 32];
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = uint32_t(atomicAdd(reinterpret_cast<unsigned long long*>(&scratch[0]), 1ull));
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = uint64_t(tile) * kLbTile;
+  prod.fill(base, n, s_val);
+  __syncthreads();
+  uint64_t excl;
+  const uint64_t tile_sum = lb_block_scan(s_val, s_warp, &excl);
   if (warp == 0) {
     uint64_t p = lb_tile_prefix(scratch + 1, tile, tile_sum, err);
     if (lane == 0) s_prefix = p;
   }
   __syncthreads();
-  uint64_t run = s_prefix + warp_excl + inc - sum;
+  uint64_t run = s_prefix + excl;
 #pragma unroll
   for (int k = 0; k < kLbItems; ++k) {
     const int idx = lb_pad(tid * kLbItems + k);
@@ -131,9 +161,9 @@ __device__ __forceinline__ void lookback_scan_tile(Producer& value, uint64_t n, 
   for (int k = 0; k < kLbItems; ++k) {
     const int local = k * kLbThreads + tid;
     const uint64_t row = base + local;
-    if (row < n) out[row] = OutT(s_val[lb_pad(local)]);
+    if (row < n) sink.store(row, s_val[lb_pad(local)]);
   }
-  if (base + kLbTile >= n && tid == 0) out[n] = OutT(s_prefix + tile_sum);
+  if (base + kLbTile >= n && tid == 0) sink.total(s_prefix + tile_sum);
 }
 
 }  // namespace mapsq

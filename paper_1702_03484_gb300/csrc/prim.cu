@@ -6,17 +6,13 @@ namespace mapsq {
 
 namespace {
 
-struct ArrayValues {
-  const uint32_t* in;
-  __device__ __forceinline__ uint32_t operator()(uint64_t i) const { return in[i]; }
-};
-
 template <class OutT>
 __global__ void __launch_bounds__(kLbThreads) prefix_sum_kernel(const uint32_t* __restrict__ in, uint64_t n,
                                                                 OutT* __restrict__ out, uint64_t* scratch,
                                                                 uint32_t* err) {
-  ArrayValues v{in};
-  lookback_scan_tile<OutT>(v, n, out, scratch, err);
+  LbArrayProducer v{in};
+  LbArraySink<OutT> sink{out, n};
+  lookback_scan_tile(v, n, sink, scratch, err);
 }
 
 __global__ void copy_u32_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint64_t n) {
