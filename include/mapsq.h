@@ -16,9 +16,10 @@
  * Tables.  A table is structure-of-arrays: ``ncols`` uint32 columns of
  * ``nrows`` rows; column c holds variable ``var[c]``.  Tables returned by the
  * library are owned by the library until ``mapsq_table_free``; their columns
- * are device pointers, 256-byte aligned.  A caller may also describe its own
+ * are device pointers (256-byte aligned, except scan results, which may be
+ * read-only slices of the triple store).  A caller may also describe its own
  * device columns in a ``mapsq_table`` it fills itself and pass it as an input;
- * such columns must be 16-byte aligned and the caller keeps ownership (never
+ * such columns must be 4-byte aligned and the caller keeps ownership (never
  * pass such a table to ``mapsq_table_free``).
  *
  * Results are multisets of rows (bag semantics, no DISTINCT); row order is
@@ -156,7 +157,9 @@ MAPSQ_API int mapsq_store_info(mapsq_ctx* ctx, uint64_t* n_triples, uint32_t* n_
 /* Partial matches of one triple pattern (Section 1, Table 1(a) and 1(b);
  * Section 2, first step of query answering).  The result has one column per
  * distinct variable, in the order s, o; a variable in both places keeps the
- * triples with s == o.  Both constants: a 0-column table of 0 or 1 rows.
+ * triples with s == o.  Both constants: a 0-column table of 0 or 1 rows.  The
+ * result may be a read-only view of the store's sorted columns (no copy); it
+ * stays valid after the store is replaced, until it is freed.
  * Synchronises.  Errors: INVALID (NULL, var id > 15), UNSUPPORTED (variable
  * predicate), OOM, BUDGET, CUDA; INVALID if no store is loaded. */
 MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_table** out);
@@ -171,6 +174,15 @@ MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_
  * than two shared variables), OOM, BUDGET, CUDA. */
 MAPSQ_API int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right, mapsq_table** out,
                const mapsq_join_opts* opts);
+
+/* Batched form: ``k`` independent joins (each as mapsq_join) evaluated
+ * together.  Every phase of the join (hash build, count, partition, write) is
+ * one launch for the whole batch, the write phase a persistent kernel fed by a
+ * device work queue, and the batch synchronises once to size all outputs, so
+ * many small joins cost about as much as one.  out[j] receives join j's table.
+ * Errors: as mapsq_join (then no table is returned). */
+MAPSQ_API int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* left,
+                               const mapsq_table* const* right, mapsq_table** out, const mapsq_join_opts* opts);
 
 /* Evaluate a BGP of ``n`` patterns (Section 2: match each pattern, join the
  * partial results after each match).  The host orders the patterns: the one
@@ -209,6 +221,11 @@ MAPSQ_API int mapsq_set_profiling(mapsq_ctx* ctx, int enable);
  * ``cap`` entries and their number to ``*n``.  Synchronises. */
 MAPSQ_API int mapsq_kernel_stats(mapsq_ctx* ctx, mapsq_kernel_stat* out, uint32_t cap, uint32_t* n);
 
+/* Restrict profiling to the kernel kind named ``name`` (as reported by
+ * mapsq_kernel_stats); NULL profiles every kind again.  Errors: INVALID
+ * (unknown name). */
+MAPSQ_API int mapsq_profile_only(mapsq_ctx* ctx, const char* name);
+
 /* Clear the per-kernel totals. */
 MAPSQ_API int mapsq_reset_stats(mapsq_ctx* ctx);
 
@@ -225,7 +242,7 @@ MAPSQ_API int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches);
  * no cudaFree, no allocating library routine.
  *
  * ``left``/``right``: caller-described tables, columns on the current device,
- * 16-byte aligned.  The smaller input may have at most 262,144 rows and the
+ * 4-byte aligned.  The smaller input may have at most 262,144 rows and the
  * larger at most 1,048,576; larger inputs give MAPSQ_ERR_INVALID before any
  * device work.  ``out_cols``: one caller-owned device buffer per output column
  * (shared variables, then the left table's other columns, then the right

@@ -95,18 +95,46 @@ int table_alloc(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, Ta
   return MAPSQ_OK;
 }
 
+int table_view(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, uint32_t* const* cols,
+               SharedBlock* owner, TableImpl** out) {
+  TableImpl* t = new (std::nothrow) TableImpl();
+  if (!t) return set_error(ctx, MAPSQ_ERR_OOM, "host allocation failed");
+  t->magic = kTableMagic;
+  t->pub.nrows = nrows;
+  t->pub.ncols = ncols;
+  t->pub.on_device = 1;
+  for (uint32_t c = 0; c < MAPSQ_MAX_VARS; ++c) {
+    t->pub.var[c] = c < ncols ? var[c] : -1;
+    t->pub.col[c] = c < ncols ? cols[c] : nullptr;
+  }
+  t->view = owner;
+  ++owner->refs;
+  ctx->live_tables.push_back(t);
+  *out = t;
+  return MAPSQ_OK;
+}
+
+void shared_release(Ctx* ctx, SharedBlock* b) {
+  if (!b || --b->refs > 0) return;
+  dev_free(ctx, b->ptr, b->bytes);
+  delete b;
+}
+
 void table_release(Ctx* ctx, TableImpl* t) {
   if (!t) return;
   auto it = std::find(ctx->live_tables.begin(), ctx->live_tables.end(), t);
   if (it == ctx->live_tables.end()) return;  // not ours, or already released
   ctx->live_tables.erase(it);
-  dev_free(ctx, t->block, t->bytes);
+  if (t->view)
+    shared_release(ctx, t->view);
+  else
+    dev_free(ctx, t->block, t->bytes);
   t->magic = 0;
   delete t;
 }
 
 int prof_begin(Ctx* ctx, int kid) {
-  if (!ctx->profiling) return -1;
+  if (!ctx->profiling || (ctx->profile_only >= 0 && ctx->profile_only != kid)) return -1;
   LaunchRecord r{kid, nullptr, nullptr, 0.0};
   for (cudaEvent_t* e : {&r.start, &r.stop}) {
     if (!ctx->free_events.empty()) {
@@ -141,6 +169,26 @@ static int drain_profile(Ctx* ctx) {
     ctx->free_events.push_back(r.stop);
   }
   ctx->pending.clear();
+  return MAPSQ_OK;
+}
+
+int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return MAPSQ_OK;
+  const int s = ctx->stage_next;
+  ctx->stage_next = (s + 1) % Ctx::kStageSlots;
+  if (ctx->stage_done[s]) MQ_CUDA(cudaEventSynchronize(ctx->stage_done[s]));
+  if (bytes > ctx->h_stage_bytes[s]) {
+    if (ctx->h_stage[s]) cudaFreeHost(ctx->h_stage[s]);
+    ctx->h_stage[s] = nullptr;
+    ctx->h_stage_bytes[s] = 0;
+    const size_t cap = std::max<size_t>(bytes, 64 << 10);
+    MQ_CUDA(cudaMallocHost(&ctx->h_stage[s], cap));
+    ctx->h_stage_bytes[s] = cap;
+  }
+  memcpy(ctx->h_stage[s], src, bytes);
+  MQ_CUDA(cudaMemcpyAsync(dst, ctx->h_stage[s], bytes, cudaMemcpyHostToDevice, ctx->stream));
+  if (!ctx->stage_done[s]) MQ_CUDA(cudaEventCreateWithFlags(&ctx->stage_done[s], cudaEventDisableTiming));
+  MQ_CUDA(cudaEventRecord(ctx->stage_done[s], ctx->stream));
   return MAPSQ_OK;
 }
 
@@ -273,6 +321,10 @@ int mapsq_destroy(mapsq_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  for (int s = 0; s < Ctx::kStageSlots; ++s) {
+    if (ctx->h_stage[s]) cudaFreeHost(ctx->h_stage[s]);
+    if (ctx->stage_done[s]) cudaEventDestroy(ctx->stage_done[s]);
+  }
   if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
   delete ctx;
   return MAPSQ_OK;
@@ -321,6 +373,17 @@ int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right
   TableImpl* t = nullptr;
   MQ_TRY(join_tables(ctx, left, right, opts, &t));
   *out = &t->pub;
+  return MAPSQ_OK;
+}
+
+int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* left, const mapsq_table* const* right,
+                     mapsq_table** out, const mapsq_join_opts* opts) {
+  if (!ctx || (k && (!left || !right || !out)))
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  std::vector<TableImpl*> t(k, nullptr);
+  MQ_TRY(join_batch(ctx, k, left, right, opts, t.data()));
+  for (uint32_t j = 0; j < k; ++j) out[j] = &t[j]->pub;
   return MAPSQ_OK;
 }
 
@@ -479,6 +542,20 @@ int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches) {
   if (!ctx || !launches) return MAPSQ_ERR_INVALID;
   *launches = ctx->launches;
   return MAPSQ_OK;
+}
+
+int mapsq_profile_only(mapsq_ctx* ctx, const char* name) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  if (!name) {
+    ctx->profile_only = -1;
+    return MAPSQ_OK;
+  }
+  for (int i = 0; i < K_COUNT_KERNELS; ++i)
+    if (strcmp(name, kKernelNames[i]) == 0) {
+      ctx->profile_only = i;
+      return MAPSQ_OK;
+    }
+  return set_error(ctx, MAPSQ_ERR_INVALID, "unknown kernel kind %s", name);
 }
 
 int mapsq_reset_stats(mapsq_ctx* ctx) {

@@ -38,13 +38,23 @@ enum KernelId {
 
 extern const char* const kKernelNames[K_COUNT_KERNELS];
 
+// A device allocation shared by its owner and the tables that alias it (the
+// triple store and the scan results that are slices of it); freed when the
+// last reference goes.
+struct SharedBlock {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int refs = 0;
+};
+
 // A library-owned table: the public struct first, so a mapsq_table* handed out
 // by the library converts back to its TableImpl.
 struct TableImpl {
   mapsq_table pub;
-  void* block;   // one allocation holding every column
+  void* block;         // one allocation holding every column, or NULL for a view
   size_t bytes;
   uint32_t magic;
+  SharedBlock* view;   // the block a view's columns alias, or NULL
 };
 constexpr uint32_t kTableMagic = 0x7AB1E5u;
 
@@ -58,8 +68,7 @@ struct Store {
   uint32_t* so_o = nullptr;
   uint32_t* os_o = nullptr;         // sorted by (p, o, s)
   uint32_t* os_s = nullptr;
-  void* block = nullptr;
-  size_t bytes = 0;
+  SharedBlock* shared = nullptr;    // the four columns' allocation
 };
 
 struct LaunchRecord {
@@ -90,7 +99,15 @@ struct mapsq_ctx {
   mapsq::Store store;
   uint32_t* d_status = nullptr;    // device status word: 0 = fine
   uint64_t* h_pinned = nullptr;    // pinned buffer for device->host reads (kPinnedWords words)
+  // ring of pinned staging buffers for host->device uploads; an upload reuses a
+  // buffer only after the copy that last read it has run
+  static constexpr int kStageSlots = 8;
+  void* h_stage[kStageSlots] = {};
+  size_t h_stage_bytes[kStageSlots] = {};
+  cudaEvent_t stage_done[kStageSlots] = {};
+  int stage_next = 0;
   bool profiling = false;
+  int profile_only = -1;          // kernel id to profile alone, or -1 for all
   uint64_t launches = 0;          // kernels launched by this context
   std::vector<mapsq::LaunchRecord> pending;
   std::vector<cudaEvent_t> free_events;
@@ -144,11 +161,19 @@ struct Scratch {
 
 // Allocate a library-owned table with room for nrows x ncols (columns 256-byte aligned).
 int table_alloc(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, TableImpl** out);
+// A table whose columns alias ``owner`` (which gains a reference).
+int table_view(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, uint32_t* const* cols,
+               SharedBlock* owner, TableImpl** out);
 void table_release(Ctx* ctx, TableImpl* t);
+void shared_release(Ctx* ctx, SharedBlock* b);
 
 // Profiling brackets around one launch (no-ops while profiling is off).
 int prof_begin(Ctx* ctx, int kid);
 void prof_end(Ctx* ctx, int rec, double alg_bytes);
+
+// Copy ``bytes`` host bytes to device memory ``dst`` on the context's stream
+// through the pinned staging buffer (waits for the previous upload to leave it).
+int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes);
 
 // Read a few 64-bit words back from the device (synchronises the stream).
 int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count);
@@ -176,9 +201,11 @@ int validate_pattern(Ctx* ctx, const mapsq_pattern& tp);
 int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* out);
 int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImpl** out);
 
-// Join (join.cu).
+// Join (join.cu): k independent joins in one batch of launches.
 int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
                 TableImpl** out);
+int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
+               const mapsq_join_opts* opts, TableImpl** out);
 
 inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 

@@ -1,5 +1,5 @@
 // MapSQ's MapReduce-based join (Algorithm 1) as a hash shuffle plus a
-// count / prefix-sum / write reduce.
+// count / prefix-sum / write reduce, for a batch of independent joins at once.
 //
 // Map: every row of both tables is mapped to its key, the shared variables
 // packed into 64 bits (one variable: the id; two: smaller variable id in the
@@ -11,11 +11,18 @@
 // each group's start, and a scatter pass writes the build side's value columns
 // grouped by key, row-major.  Reduce: every row of the other table (the probe
 // side) looks its key up and counts its matches (the size of its LEFT x RIGHT
-// cross product) inside a single-pass look-back prefix sum that gives each probe
-// row its output range; a partition pass finds, for every output tile, the
-// probe rows that feed it; the write pass then emits every LEFT x RIGHT pair
-// exactly once, partitioned by output position so that skewed keys are spread
-// over all SMs, with 16-byte streaming stores into each output column.
+// cross product); tile-local prefix sums and a scan of the tile totals give
+// every probe row its output range; a partition pass finds, for every output
+// tile, the probe rows that feed it; the write pass then emits every LEFT x
+// RIGHT pair exactly once, partitioned by output position so that skewed keys
+// are spread over all SMs.
+//
+// Batching: every phase is one launch for all the joins of a batch.  Its work
+// items (a join and a tile of that join) are numbered across the batch; a CTA
+// finds its join by a binary search of the per-join item offsets.  The write
+// phase is a persistent kernel that takes items from a device work counter.
+// A batch synchronises once, to size its outputs (twice when large build sides
+// need a distinct-key estimate).  A single join is a batch of one.
 //
 // Output layout (Table 1(c)): shared variables in ascending id, then the left
 // table's other columns, then the right table's.  No shared variable: the cross
@@ -34,27 +41,31 @@ namespace {
 
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr uint32_t kNoSlot = 0xffffffffu;
-constexpr int kThreads = 256;                                        // threads per CTA of the probe and write passes
-constexpr int kProbeTile = 2048;                                     // probe rows per count tile
-constexpr int kProbeItems = kProbeTile / kThreads;                   // probe rows per thread
-constexpr int kWriteRows = 16;                                       // output rows per thread per write tile
-constexpr int kWriteTile = kThreads * kWriteRows;                    // output rows per write tile
-constexpr int kStageRows = 1800;                                     // probe rows staged per write tile (48 KB of static shared memory in all)
-constexpr int kMapWords = kWriteTile + kWriteTile / 32;              // row map, padded one word per 32
+constexpr int kThreads = 256;                          // threads per CTA
+constexpr int kRowTile = 2048;                         // rows per work item (build, slots, probe)
+constexpr int kRowItems = kRowTile / kThreads;         // rows per thread
+constexpr int kWriteRows = 16;                         // output rows per thread per write tile
+constexpr int kWriteTile = kThreads * kWriteRows;      // output rows per write tile
+constexpr int kStageRows = 1800;                       // probe rows staged per write tile (48 KB of shared memory in all)
+constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
 constexpr int kHllBits = 12;
 constexpr int kHllRegs = 1 << kHllBits;
-constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;                 // smaller build sides size the table by rows
+constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides size the table by rows
+constexpr int kBucket = 4;
+constexpr int kPhases = 8;
+
+enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS };
 
 // Open-addressing table of the build side's distinct keys: ``keys`` holds M
 // 64-bit keys in buckets of 4 (one 32-byte sector), probed bucket after bucket
 // from the key's home bucket; ``group`` holds, per slot, the key group's size
-// and its first row in the grouped build values.  The all-ones key marks an
-// empty slot; the one real key equal to it uses the extra group entry M.
-constexpr int kBucket = 4;
-
+// and its first row inside its tile of kRowTile slots (the tile's start is
+// slot_base[slot / kRowTile]).  The all-ones key marks an empty slot; the one
+// real key equal to it uses the extra group entry M.
 struct HashTable {
   uint64_t* keys;  // M entries, M a multiple of kBucket
-  uint2* group;    // M + 1 entries: {count, begin}
+  uint2* group;    // M + 1 entries: {count, begin within the slot tile}
+  uint64_t* slot_base;
   uint32_t M;
 };
 
@@ -62,6 +73,42 @@ struct KeyCols {
   const uint32_t* c0;  // variable with the smaller id (high word when two)
   const uint32_t* c1;  // nullptr for a single-variable key
 };
+
+// Everything one join of a batch needs on the device.
+struct JoinDesc {
+  KeyCols bk, pk;                 // build and probe keys
+  uint64_t nb, np;                // build and probe rows
+  HashTable t;
+  uint32_t* hll;                  // kHllRegs registers, or NULL
+  uint32_t* slot_of;              // nb: slot of each build row
+  uint32_t* rank_of;              // nb: rank inside its group
+  uint64_t* slot_total;           // per slot tile: sum of its group sizes
+  const uint32_t* bsrc[MAPSQ_MAX_VARS];  // build value columns
+  int nbv;                        // their number (row-major stride of ``grouped``)
+  uint32_t* grouped;              // nb * nbv: build values grouped by key
+  uint32_t* local;                // np: output offset of each probe row inside its tile
+  uint32_t* pbeg;                 // np: group start of each probe row
+  uint64_t* tile_total;           // per probe tile: its output rows
+  uint64_t* tile_base;            // per probe tile + 1: output offset of the tile (last = T)
+  uint64_t T;                     // output rows (set after the count phase)
+  uint64_t* part;                 // output tiles + 1: first probe row of each output tile
+  const uint32_t* src[MAPSQ_MAX_VARS];  // output column c: probe column, or build values + j
+  uint32_t* out[MAPSQ_MAX_VARS];
+  uint32_t from_build;            // bit c: column c comes from the build side
+  int ncols;
+  int cross;                      // no shared variable: output row r pairs probe row r / nb with build row r % nb
+  int hash;                       // shared variables and both sides non-empty: the hash path runs
+};
+
+// Item offsets of one phase: join j owns items [first[j], first[j + 1]).
+__device__ __forceinline__ uint32_t item_join(const uint64_t* first, uint32_t k, uint64_t item) {
+  uint32_t lo = 0, hi = k;  // last j with first[j] <= item
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (first[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 // Key columns are streamed once per pass: evict-first loads keep the hash table
 // resident in L2.
@@ -87,6 +134,14 @@ __device__ __forceinline__ uint32_t home_bucket(uint64_t key, uint32_t M) {
   return uint32_t((uint64_t(h * 0x85ebca6bu) * uint64_t(M / kBucket)) >> 32);
 }
 
+__device__ __forceinline__ void load_bucket(const HashTable& t, uint64_t key, uint32_t* b, ulonglong2* k01,
+                                            ulonglong2* k23) {
+  *b = home_bucket(key, t.M);
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.keys + uint64_t(*b) * kBucket);
+  *k01 = __ldg(p);
+  *k23 = __ldg(p + 1);
+}
+
 // Slot of ``key`` in the table, or kNoSlot, starting from its home bucket
 // whose keys are already loaded (k01 = slots 0-1, k23 = slots 2-3).
 __device__ __forceinline__ uint32_t find_slot(const HashTable& t, uint64_t key, uint32_t b, ulonglong2 k01,
@@ -94,7 +149,7 @@ __device__ __forceinline__ uint32_t find_slot(const HashTable& t, uint64_t key, 
   if (key == kEmptyKey) return t.M;
   const uint32_t nbk = t.M / kBucket;
   for (uint32_t it = 0; it < nbk; ++it) {
-    // first slot of the bucket holding the key or empty decides
+    // the first slot of the bucket holding the key or empty decides
     const uint32_t hit = uint32_t(k01.x == key) | uint32_t(k01.y == key) << 1 | uint32_t(k23.x == key) << 2 |
                          uint32_t(k23.y == key) << 3;
     const uint32_t emp = uint32_t(k01.x == kEmptyKey) | uint32_t(k01.y == kEmptyKey) << 1 |
@@ -111,31 +166,61 @@ __device__ __forceinline__ uint32_t find_slot(const HashTable& t, uint64_t key, 
   return kNoSlot;
 }
 
-__device__ __forceinline__ void load_bucket(const HashTable& t, uint64_t key, uint32_t* b, ulonglong2* k01,
-                                            ulonglong2* k23) {
-  *b = home_bucket(key, t.M);
-  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.keys + uint64_t(*b) * kBucket);
-  *k01 = __ldg(p);
-  *k23 = __ldg(p + 1);
+// Group start (over the whole build side) of slot s.
+__device__ __forceinline__ uint32_t group_begin(const HashTable& t, uint32_t s, uint32_t local_begin) {
+  return local_begin + uint32_t(t.slot_base[s / kRowTile]);
 }
+
+// Block-wide exclusive scan of one value per thread (row order = thread order
+// of ``vals`` laid out kRowItems consecutive rows per thread); returns the
+// thread's exclusive prefix and the block total.
+__device__ __forceinline__ uint64_t block_scan(uint64_t sum, uint64_t* s_warp, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t inc = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t x = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += x;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  uint64_t before = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) {
+    const uint64_t x = s_warp[w];
+    if (w < warp) before += x;
+    tot += x;
+  }
+  *total = tot;
+  return before + inc - sum;
+}
+
+// ------------------------------------------------------------------ phases
 
 // HyperLogLog sketch of the build keys (Flajolet, Fusy, Gandouet, Meunier,
 // 2007): 2^12 registers hold the largest leading-zero count + 1 seen among the
 // hashes routed to them.  The input is salted so the hash is independent of the
 // table's.
-__global__ void hll_kernel(KeyCols k, uint64_t n, uint32_t* __restrict__ regs) {
+__global__ void __launch_bounds__(kThreads) hll_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                      uint32_t k) {
   __shared__ uint32_t s[kHllRegs];
-  for (int j = threadIdx.x; j < kHllRegs; j += blockDim.x) s[j] = 0;
+  const uint32_t j = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[j];
+  const uint64_t base = (blockIdx.x - first[j]) * kRowTile;
+  for (int r = threadIdx.x; r < kHllRegs; r += kThreads) s[r] = 0;
   __syncthreads();
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
-    uint64_t h = mix_key(load_key(k, i) ^ 0x9e3779b97f4a7c15ull);
-    uint32_t idx = uint32_t(h >> (64 - kHllBits));
-    uint64_t w = (h << kHllBits) | (1ull << (kHllBits - 1));
-    atomicMax(&s[idx], uint32_t(__clzll(w) + 1));
+#pragma unroll
+  for (int it = 0; it < kRowItems; ++it) {
+    const uint64_t i = base + uint64_t(it) * kThreads + threadIdx.x;
+    if (i < d.nb) {
+      const uint64_t h = mix_key(load_key(d.bk, i) ^ 0x9e3779b97f4a7c15ull);
+      const uint64_t w = (h << kHllBits) | (1ull << (kHllBits - 1));
+      atomicMax(&s[h >> (64 - kHllBits)], uint32_t(__clzll(w) + 1));
+    }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < kHllRegs; j += blockDim.x)
-    if (s[j]) atomicMax(&regs[j], s[j]);
+  for (int r = threadIdx.x; r < kHllRegs; r += kThreads)
+    if (s[r]) atomicMax(&d.hll[r], s[r]);
 }
 
 double hll_estimate(const uint32_t* regs) {
@@ -152,36 +237,39 @@ double hll_estimate(const uint32_t* regs) {
 }
 
 // Insert every build row's key; slot_of[i] = its group's slot, rank_of[i] = its
-// rank inside the group, counted in the group table.
-__global__ void hash_insert_kernel(KeyCols bk, uint64_t nb, HashTable t, uint32_t* __restrict__ slot_of,
-                                   uint32_t* __restrict__ rank_of, uint32_t* __restrict__ status) {
+// rank inside the group, counted in the group table (warp-aggregated).
+__global__ void __launch_bounds__(kThreads) hash_insert_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                              uint32_t k, uint32_t* __restrict__ status) {
+  const uint32_t j = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[j];
+  const HashTable t = d.t;
+  const uint64_t base = (blockIdx.x - first[j]) * kRowTile;
   const unsigned lane = threadIdx.x & 31;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint32_t nbk = t.M / kBucket;
-  for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x; base < nb; base += stride) {
-    uint64_t i = base + threadIdx.x;
-    bool valid = i < nb;
+  for (int it = 0; it < kRowItems; ++it) {
+    const uint64_t i = base + uint64_t(it) * kThreads + threadIdx.x;
+    const bool valid = i < d.nb;
     uint32_t s = kNoSlot;
     if (valid) {
-      const uint64_t key = load_key(bk, i);
+      const uint64_t key = load_key(d.bk, i);
       if (key == kEmptyKey) {
         s = t.M;
       } else {
         uint32_t b = home_bucket(key, t.M);
-        for (uint32_t it = 0; it < nbk && s == kNoSlot; ++it) {
+        for (uint32_t n = 0; n < nbk && s == kNoSlot; ++n) {
           uint64_t* bkt = t.keys + uint64_t(b) * kBucket;
           const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt));
           const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt) + 1);
-          const uint64_t k[4] = {k01.x, k01.y, k23.x, k23.y};
+          const uint64_t kk[4] = {k01.x, k01.y, k23.x, k23.y};
 #pragma unroll
-          for (int j = 0; j < kBucket; ++j) {
+          for (int q = 0; q < kBucket; ++q) {
             if (s != kNoSlot) break;
-            if (k[j] == key) {
-              s = b * kBucket + j;
-            } else if (k[j] == kEmptyKey) {
-              const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(bkt + j),
+            if (kk[q] == key) {
+              s = b * kBucket + q;
+            } else if (kk[q] == kEmptyKey) {
+              const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(bkt + q),
                                                         (unsigned long long)kEmptyKey, (unsigned long long)key);
-              if (prev == kEmptyKey || prev == key) s = b * kBucket + j;
+              if (prev == kEmptyKey || prev == key) s = b * kBucket + q;
             }
           }
           b = b + 1 == nbk ? 0 : b + 1;
@@ -189,211 +277,71 @@ __global__ void hash_insert_kernel(KeyCols bk, uint64_t nb, HashTable t, uint32_
         if (s == kNoSlot) atomicOr(status, 1u);  // table full: the host rebuilds it larger
       }
     }
-    // warp-aggregated group ranks: one atomic per distinct slot in the warp
-    unsigned peers = __match_any_sync(0xffffffffu, s);
-    int leader = __ffs(peers) - 1;
+    const unsigned peers = __match_any_sync(0xffffffffu, s);
+    const int leader = __ffs(peers) - 1;
     uint32_t base_rank = 0;
     if (lane == unsigned(leader) && valid && s != kNoSlot) base_rank = atomicAdd(&t.group[s].x, __popc(peers));
     base_rank = __shfl_sync(0xffffffffu, base_rank, leader);
     if (valid) {
-      slot_of[i] = s;
-      rank_of[i] = base_rank + __popc(peers & ((1u << lane) - 1u));
+      d.slot_of[i] = s;
+      d.rank_of[i] = base_rank + __popc(peers & ((1u << lane) - 1u));
     }
   }
 }
 
-// Group starts: exclusive prefix sum of the groups' sizes, written next to
-// them (look-back scan over the M + 1 group entries).
-struct GroupCounts {
-  const uint2* group;
-  __device__ __forceinline__ void fill(uint64_t base, uint64_t n, uint64_t* s) const {
-#pragma unroll 4
-    for (int k = 0; k < kLbItems; ++k) {
-      const int local = k * kLbThreads + threadIdx.x;
-      const uint64_t row = base + local;
-      s[lb_pad(local)] = row < n ? uint64_t(group[row].x) : 0ull;
-    }
-  }
-};
-
-struct GroupStarts {
-  uint2* group;
-  __device__ __forceinline__ void store(uint64_t row, uint64_t v) const {
-    if (group[row].x) group[row].y = uint32_t(v);
-  }
-  __device__ __forceinline__ void total(uint64_t) const {}
-};
-
-__global__ void __launch_bounds__(kLbThreads) slot_prefix_kernel(uint2* __restrict__ group, uint64_t n, uint64_t* lb,
-                                                                 uint32_t* err) {
-  GroupCounts c{group};
-  GroupStarts s{group};
-  lookback_scan_tile(c, n, s, lb, err);
-}
-
-struct BuildValues {
-  const uint32_t* src[MAPSQ_MAX_VARS];
-  int n;
-};
-
-constexpr int kScatterRows = 4;  // build rows per thread, loads issued together
-
-// Group the build side's value columns by key, row-major: row i's values go to
-// grouped[(begin of its group + rank) * n + j].
-__global__ void hash_scatter_kernel(BuildValues v, uint64_t nb, const uint32_t* __restrict__ slot_of,
-                                    const uint32_t* __restrict__ rank_of, const uint2* __restrict__ group,
-                                    uint32_t* __restrict__ grouped) {
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kScatterRows;
-  for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x * kScatterRows + threadIdx.x; base < nb; base += stride) {
-    uint32_t s[kScatterRows], rk[kScatterRows], beg[kScatterRows];
-#pragma unroll
-    for (int k = 0; k < kScatterRows; ++k) {
-      const uint64_t i = base + uint64_t(k) * blockDim.x;
-      s[k] = i < nb ? __ldcs(slot_of + i) : kNoSlot;
-      rk[k] = i < nb ? __ldcs(rank_of + i) : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < kScatterRows; ++k) beg[k] = s[k] != kNoSlot ? group[s[k]].y : 0u;
-    for (int c = 0; c < v.n; ++c) {
-      uint32_t x[kScatterRows];
-#pragma unroll
-      for (int k = 0; k < kScatterRows; ++k) {
-        const uint64_t i = base + uint64_t(k) * blockDim.x;
-        x[k] = s[k] != kNoSlot ? __ldcs(v.src[c] + i) : 0u;
-      }
-#pragma unroll
-      for (int k = 0; k < kScatterRows; ++k)
-        if (s[k] != kNoSlot) grouped[uint64_t(beg[k] + rk[k]) * uint32_t(v.n) + c] = x[k];
-    }
-  }
-}
-
-// Probes ``kProbeItems`` rows per thread, four lookups in flight at a time:
-// out_cnt[k] / out_beg[k] = match count and group start of row
-// base + k * kThreads + threadIdx.x (0 past np).
-__device__ __forceinline__ void probe_rows(const KeyCols& pk, uint64_t np, const HashTable& t, uint64_t base,
-                                           uint32_t* out_cnt, uint32_t* out_beg) {
-  constexpr int H = 4;
-#pragma unroll
-  for (int h0 = 0; h0 < kProbeItems; h0 += H) {
-    uint64_t key[H];
-    uint32_t b[H], s[H];
-    ulonglong2 k01[H], k23[H];
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const uint64_t row = base + uint64_t(h0 + k) * kThreads + threadIdx.x;
-      key[k] = row < np ? load_key(pk, row) : kEmptyKey;
-    }
-#pragma unroll
-    for (int k = 0; k < H; ++k)
-      if (key[k] != kEmptyKey) load_bucket(t, key[k], &b[k], &k01[k], &k23[k]);
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const uint64_t row = base + uint64_t(h0 + k) * kThreads + threadIdx.x;
-      s[k] = row < np ? find_slot(t, key[k], b[k], k01[k], k23[k]) : kNoSlot;
-    }
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      const uint2 g = s[k] != kNoSlot ? t.group[s[k]] : make_uint2(0u, 0u);
-      out_cnt[h0 + k] = g.x;
-      out_beg[h0 + k] = g.y;
-    }
-  }
-}
-
-// Count pass, tile-local: every probe row's match count and group start, the
-// exclusive prefix sums of the counts inside its tile of kProbeTile rows, and
-// the tile's total.  Output offsets are tile_base[row / kProbeTile] +
-// local[row] once the tile totals are scanned; no CTA waits for another.
-template <class OffT>
-__global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(KeyCols pk, uint64_t np, HashTable t,
-                                                                  OffT* __restrict__ local,
-                                                                  uint32_t* __restrict__ pbeg,
-                                                                  uint64_t* __restrict__ tile_total,
-                                                                  uint32_t* __restrict__ status) {
-  __shared__ uint32_t s_cnt[kProbeTile + kProbeTile / 32];
+// Slot tiles: the group starts inside each tile of kRowTile slots (written into
+// group[].y) and the tile's total.
+__global__ void __launch_bounds__(kThreads) slot_scan_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                            uint32_t k) {
   __shared__ uint64_t s_warp[kThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t base = uint64_t(blockIdx.x) * kProbeTile;
-  auto pad = [](int i) { return i + (i >> 5); };
-  {
-    uint32_t cnt[kProbeItems], beg[kProbeItems];
-    probe_rows(pk, np, t, base, cnt, beg);
-#pragma unroll
-    for (int k = 0; k < kProbeItems; ++k) {
-      const int loc = k * kThreads + tid;
-      if (base + loc < np) __stcs(pbeg + base + loc, beg[k]);
-      s_cnt[pad(loc)] = cnt[k];
-    }
-  }
-  __syncthreads();
-  // block scan: each thread owns kProbeItems consecutive rows
-  uint32_t v[kProbeItems];
+  const uint32_t j = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[j];
+  const uint64_t base = (blockIdx.x - first[j]) * kRowTile, n = uint64_t(d.t.M) + 1;
+  uint32_t c[kRowItems];
   uint64_t sum = 0;
 #pragma unroll
-  for (int k = 0; k < kProbeItems; ++k) {
-    v[k] = s_cnt[pad(tid * kProbeItems + k)];
-    sum += v[k];
+  for (int it = 0; it < kRowItems; ++it) {
+    const uint64_t s = base + uint64_t(threadIdx.x) * kRowItems + it;
+    c[it] = s < n ? d.t.group[s].x : 0u;
+    sum += c[it];
   }
-  uint64_t inc = sum;
+  uint64_t total;
+  uint64_t run = block_scan(sum, s_warp, &total);
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint64_t x = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d) inc += x;
+  for (int it = 0; it < kRowItems; ++it) {
+    const uint64_t s = base + uint64_t(threadIdx.x) * kRowItems + it;
+    if (s < n && c[it]) d.t.group[s].y = uint32_t(run);
+    run += c[it];
   }
-  if (lane == 31) s_warp[warp] = inc;
-  __syncthreads();
-  uint64_t run = inc - sum, tile_sum = 0;
-#pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) {
-    const uint64_t x = s_warp[w];
-    if (w < warp) run += x;
-    tile_sum += x;
-  }
-  // local offsets, written back in row order through shared memory, half a tile at a time
-  __syncthreads();
-  uint64_t* s_off = reinterpret_cast<uint64_t*>(s_cnt);
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    if ((tid * kProbeItems) / (kProbeTile / 2) == half) {
-#pragma unroll
-      for (int k = 0; k < kProbeItems; ++k) {
-        s_off[(tid * kProbeItems + k) % (kProbeTile / 2)] = run;
-        run += v[k];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kProbeItems / 2; ++k) {
-      const int loc = half * (kProbeTile / 2) + k * kThreads + tid;
-      const uint64_t row = base + loc;
-      if (row < np) __stcs(local + row, OffT(s_off[loc - half * (kProbeTile / 2)]));
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    tile_total[blockIdx.x] = tile_sum;
-    if (sizeof(OffT) < 8 && tile_sum > 0xffffffffull) atomicOr(status, 4u);  // needs 64-bit local offsets
-  }
+  if (threadIdx.x == 0) d.slot_total[blockIdx.x - first[j]] = total;
 }
 
-// Exclusive scan of the count tiles' totals by one CTA: tile_base[t], and the
-// join's row count in tile_base[ntiles].
-__global__ void __launch_bounds__(1024) tile_scan_kernel(const uint64_t* __restrict__ tile_total, uint64_t ntiles,
-                                                        uint64_t* __restrict__ tile_base) {
+// Exclusive scans of per-tile totals, one CTA per join: slot tile starts
+// (which = 0) or probe tile output offsets with the join's row count last
+// (which = 1).
+__global__ void __launch_bounds__(1024) tiles_scan_kernel(JoinDesc* __restrict__ jd, uint32_t k, int which,
+                                                         uint64_t* __restrict__ totals_out) {
   __shared__ uint64_t s_warp[32];
   __shared__ uint64_t s_carry;
+  JoinDesc& d = jd[blockIdx.x];
+  if (!d.hash) {
+    if (which == 1 && threadIdx.x == 0) totals_out[blockIdx.x] = d.cross ? d.np * d.nb : 0;
+    return;
+  }
+  const uint64_t n = which == 0 ? (uint64_t(d.t.M) + kRowTile) / kRowTile : (d.np + kRowTile - 1) / kRowTile;
+  const uint64_t* tot = which == 0 ? d.slot_total : d.tile_total;
+  uint64_t* out = which == 0 ? d.t.slot_base : d.tile_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  for (uint64_t b = 0; b < ntiles; b += blockDim.x) {
+  for (uint64_t b = 0; b < n; b += blockDim.x) {
     const uint64_t i = b + threadIdx.x;
-    const uint64_t v = i < ntiles ? tile_total[i] : 0ull;
+    const uint64_t v = i < n ? tot[i] : 0ull;
     uint64_t inc = v;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      uint64_t x = __shfl_up_sync(0xffffffffu, inc, d);
-      if (lane >= d) inc += x;
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint64_t x = __shfl_up_sync(0xffffffffu, inc, dd);
+      if (lane >= dd) inc += x;
     }
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
@@ -402,208 +350,293 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const uint64_t* __restr
       if (w < warp) before += s_warp[w];
       chunk += s_warp[w];
     }
-    if (i < ntiles) tile_base[i] = before + inc - v;
+    if (i < n) out[i] = before + inc - v;
     __syncthreads();
     if (threadIdx.x == 0) s_carry += chunk;
     __syncthreads();
   }
-  if (threadIdx.x == 0) tile_base[ntiles] = s_carry;
+  if (threadIdx.x == 0) {
+    out[n] = s_carry;
+    if (which == 1) totals_out[blockIdx.x] = s_carry;
+  }
 }
 
-// Output offset of probe row i (i == np gives the row count).
-template <class OffT>
-struct Offsets {
-  const OffT* local;
-  const uint64_t* tile_base;
-  uint64_t np, T;
-  __device__ __forceinline__ uint64_t at(uint64_t i) const {
-    return i < np ? tile_base[i / kProbeTile] + uint64_t(local[i]) : T;
-  }
-  // the probe row whose output range holds output row v, searched in [lo, hi)
-  __device__ __forceinline__ uint64_t row_of(uint64_t v, uint64_t lo, uint64_t hi) const {
-    while (lo < hi) {
-      uint64_t mid = lo + (hi - lo) / 2;
-      if (at(mid) <= v) lo = mid + 1; else hi = mid;
+// Group the build side's value columns by key, row-major: row i's values go to
+// grouped[(start of its group + rank) * nbv + c].
+__global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                               uint32_t k) {
+  const uint32_t j = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[j];
+  const uint64_t base = (blockIdx.x - first[j]) * kRowTile;
+  const int nbv = d.nbv;
+#pragma unroll 1
+  for (int h0 = 0; h0 < kRowItems; h0 += 4) {
+    uint32_t s[4], pos[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t i = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+      s[q] = i < d.nb ? __ldcs(d.slot_of + i) : kNoSlot;
+      pos[q] = i < d.nb ? __ldcs(d.rank_of + i) : 0u;
     }
-    return lo - 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (s[q] != kNoSlot) pos[q] += group_begin(d.t, s[q], d.t.group[s[q]].y);
+    for (int c = 0; c < nbv; ++c) {
+      uint32_t x[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t i = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+        x[q] = s[q] != kNoSlot ? __ldcs(d.bsrc[c] + i) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (s[q] != kNoSlot) d.grouped[uint64_t(pos[q]) * uint32_t(nbv) + c] = x[q];
+    }
   }
-};
+}
+
+// Count phase, tile-local: every probe row's match count and group start (four
+// lookups in flight per thread), the exclusive prefix sums of the counts inside
+// its tile of kRowTile rows (``local``), and the tile's total.  No CTA waits
+// for another; the tile totals are scanned afterwards.
+__global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc* __restrict__ jd,
+                                                                  const uint64_t* first, uint32_t k,
+                                                                  uint32_t* __restrict__ status) {
+  __shared__ uint32_t s_cnt[kRowTile + kRowTile / 32];
+  __shared__ uint64_t s_warp[kThreads / 32];
+  const uint32_t jj = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[jj];
+  const HashTable t = d.t;
+  const uint64_t tile = blockIdx.x - first[jj];
+  const uint64_t base = tile * kRowTile;
+  const uint64_t np = d.np;
+  auto pad = [](int i) { return i + (i >> 5); };
+#pragma unroll
+  for (int h0 = 0; h0 < kRowItems; h0 += 4) {
+    uint64_t key[4];
+    uint32_t b[4], s[4];
+    ulonglong2 k01[4], k23[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+      key[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (key[q] != kEmptyKey) load_bucket(t, key[q], &b[q], &k01[q], &k23[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+      s[q] = row < np ? find_slot(t, key[q], b[q], k01[q], k23[q]) : kNoSlot;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int loc = (h0 + q) * kThreads + threadIdx.x;
+      const uint64_t row = base + loc;
+      const uint2 g = s[q] != kNoSlot ? t.group[s[q]] : make_uint2(0u, 0u);
+      if (row < np) __stcs(d.pbeg + row, g.x ? group_begin(t, s[q], g.y) : 0u);
+      s_cnt[pad(loc)] = g.x;
+    }
+  }
+  __syncthreads();
+  uint32_t v[kRowItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    v[q] = s_cnt[pad(threadIdx.x * kRowItems + q)];
+    sum += v[q];
+  }
+  uint64_t tile_sum;
+  uint64_t run = block_scan(sum, s_warp, &tile_sum);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    s_cnt[pad(threadIdx.x * kRowItems + q)] = uint32_t(run);
+    run += v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    const int loc = q * kThreads + threadIdx.x;
+    if (base + loc < np) __stcs(d.local + base + loc, s_cnt[pad(loc)]);
+  }
+  if (threadIdx.x == 0) {
+    d.tile_total[tile] = tile_sum;
+    if (tile_sum > 0xffffffffull) atomicOr(status, 4u);  // tile-local offsets would not fit in 32 bits
+  }
+}
+
+// Output offset of probe row i of a join (i == np gives its row count).
+__device__ __forceinline__ uint64_t off_at(const JoinDesc& d, uint64_t i) {
+  return i < d.np ? d.tile_base[i / kRowTile] + d.local[i] : d.T;
+}
 
 template <class T>
 __device__ __forceinline__ uint64_t upper_bound_t(const T* a, uint64_t lo, uint64_t hi, uint64_t v) {
   while (lo < hi) {
-    uint64_t mid = lo + (hi - lo) / 2;
+    const uint64_t mid = lo + (hi - lo) / 2;
     if (uint64_t(a[mid]) <= v) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
-// Merge-path partition of the output: part[t] = the probe row whose output
-// range holds output row min(t * kWriteTile, T - 1), for t in [0, ntiles]:
-// first the count tile (search over tile bases), then the row inside it.
-template <class OffT>
-__global__ void write_partition_kernel(Offsets<OffT> off, uint64_t count_tiles, uint64_t ntiles,
-                                       uint64_t* __restrict__ part) {
-  for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t <= ntiles; t += uint64_t(gridDim.x) * blockDim.x) {
-    const uint64_t v = min(t * uint64_t(kWriteTile), off.T - 1);
-    const uint64_t ct = upper_bound_t(off.tile_base, 0, count_tiles + 1, v) - 1;
-    const uint64_t lo = ct * kProbeTile, hi = min(lo + kProbeTile, off.np);
-    part[t] = lo + upper_bound_t(off.local + lo, 0, hi - lo, v - off.tile_base[ct]) - 1;
+// The probe row whose output range holds output row v, searched in [lo, hi).
+__device__ __forceinline__ uint64_t row_of(const JoinDesc& d, uint64_t v, uint64_t lo, uint64_t hi) {
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (off_at(d, mid) <= v) lo = mid + 1; else hi = mid;
   }
+  return lo - 1;
 }
 
-template <class OffT>
-struct WriteParams {
-  Offsets<OffT> off;
-  const uint64_t* part;  // probe row of each output tile's first row (ntiles + 1)
-  const uint32_t* pbeg;  // group start of each probe row
-  uint64_t np, nb, T;
-  const uint32_t* src[MAPSQ_MAX_VARS];
-  uint32_t* out[MAPSQ_MAX_VARS];
-  uint32_t from_build;   // bit c: column c comes from the build side
-  uint32_t bstride;      // words between consecutive build rows in src (row-major grouped values)
-  int ncols;
-};
+// Merge-path partition of each join's output: part[t] = the probe row whose
+// output range holds output row min(t * kWriteTile, T - 1), t in [0, ntiles]:
+// first its probe tile (search over tile offsets), then the row inside it.
+__global__ void __launch_bounds__(kThreads) write_partition_kernel(const JoinDesc* __restrict__ jd,
+                                                                  const uint64_t* first, uint32_t k) {
+  const uint32_t j = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[j];
+  const uint64_t t = (blockIdx.x - first[j]) * kThreads + threadIdx.x;
+  const uint64_t ntiles = (d.T + kWriteTile - 1) / kWriteTile;
+  if (t > ntiles) return;
+  const uint64_t v = min(t * uint64_t(kWriteTile), d.T - 1);
+  const uint64_t nt = (d.np + kRowTile - 1) / kRowTile;
+  const uint64_t ct = upper_bound_t(d.tile_base, 0, nt + 1, v) - 1;
+  const uint64_t lo = ct * kRowTile, hi = min(lo + kRowTile, d.np);
+  d.part[t] = lo + upper_bound_t(d.local + lo, 0, hi - lo, v - d.tile_base[ct]) - 1;
+}
 
 __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t v) {
   while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
+    const uint32_t mid = (lo + hi) >> 1;
     if (a[mid] <= v) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
-// Write pass: CTA tiles of kWriteTile output rows.  (1) The probe rows feeding
-// the tile get their output offsets (relative to the tile) and group starts
-// staged in shared memory.  (2) Every thread maps 16 consecutive output rows to
-// (probe row, build row) with one 32-bit search and a short walk, into shared
-// memory.  (3) Every thread takes 16 rows striped over the block (a row per
-// lane), reads their map entries once, and for every column issues the 16
-// gathers before the 16 coalesced streaming stores.
-template <class OffT>
-__global__ void __launch_bounds__(kThreads, 4) join_write_kernel(WriteParams<OffT> p) {
+// One output column of a tile: row j * kThreads + tid takes src[idx[j] * stride];
+// the gathers are issued before the coalesced streaming stores.
+template <bool kFull>
+__device__ __forceinline__ void write_column(const uint32_t* __restrict__ src, const uint32_t (&idx)[kWriteRows],
+                                             uint32_t stride, uint32_t* __restrict__ dst, uint32_t n) {
+  uint32_t x[kWriteRows];
+#pragma unroll
+  for (int j = 0; j < kWriteRows; ++j)
+    x[j] = kFull || uint32_t(j) * kThreads + threadIdx.x < n ? __ldg(src + uint64_t(idx[j]) * stride) : 0u;
+  uint32_t* dd = dst + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kWriteRows; ++j)
+    if (kFull || uint32_t(j) * kThreads + threadIdx.x < n) __stcs(dd + j * kThreads, x[j]);
+}
+
+// Write phase, persistent: CTAs take write items (a join and one of its output
+// tiles of kWriteTile rows) from a device work counter until none are left.
+// Per item: (1) the probe rows feeding the tile get their output offsets
+// (relative to the tile) and group starts staged in shared memory; (2) every
+// thread maps 16 consecutive output rows to (probe row, build row) with one
+// 32-bit search and a short walk, into a padded row map; (3) every thread takes
+// 16 rows striped over the block (a row per lane), reads their map entries once
+// per side, and writes the columns with coalesced streaming stores.
+__global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                                 uint32_t k, unsigned long long* __restrict__ queue) {
   __shared__ uint32_t s_rel[kStageRows + 1];
   __shared__ uint32_t s_beg[kStageRows];
   __shared__ uint32_t s_pk[kMapWords];  // probe row of each output row (relative to the tile's first)
   __shared__ uint32_t s_bk[kMapWords];  // build row of each output row
+  __shared__ uint32_t s_skip;
+  __shared__ unsigned long long s_item;
   // row q lives at q + q / 32: conflict-free both for the 16 consecutive rows a
   // thread maps and for the rows striped over the block that it gathers
   auto mi = [](uint32_t q) { return q + (q >> 5); };
-  __shared__ uint32_t s_skip;
-  const uint64_t ntiles = (p.T + kWriteTile - 1) / kWriteTile;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const uint64_t nitems = first[k];
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1ull);
+    __syncthreads();
+    const uint64_t item = s_item;
+    if (item >= nitems) break;
+    const uint32_t jj = item_join(first, k, item);
+    const JoinDesc& d = jd[jj];
+    const uint64_t tile = item - first[jj];
     const uint64_t t0 = tile * kWriteTile;
-    const uint32_t n = uint32_t(min(uint64_t(kWriteTile), p.T - t0));
-    const uint64_t ilo = p.part[tile];
-    const uint64_t nst = p.part[tile + 1] - ilo + 1;  // probe rows ilo .. part[tile + 1] can feed this tile
+    const uint32_t n = uint32_t(min(uint64_t(kWriteTile), d.T - t0));
+    const uint64_t ilo = d.part[tile];
+    const uint64_t nst = d.part[tile + 1] - ilo + 1;  // probe rows ilo .. part[tile + 1] can feed this tile
     const uint32_t q0 = threadIdx.x * kWriteRows;
     if (nst <= kStageRows) {
       const uint32_t ns = uint32_t(nst);
-      for (uint32_t k = threadIdx.x; k <= ns; k += kThreads) {
-        const uint64_t v = p.off.at(ilo + k);
-        s_rel[k] = v <= t0 ? 0u : uint32_t(min(v - t0, uint64_t(kWriteTile)));
+      for (uint32_t r = threadIdx.x; r <= ns; r += kThreads) {
+        const uint64_t v = off_at(d, ilo + r);
+        s_rel[r] = v <= t0 ? 0u : uint32_t(min(v - t0, uint64_t(kWriteTile)));
       }
-      for (uint32_t k = threadIdx.x; k < ns; k += kThreads) s_beg[k] = p.pbeg[ilo + k];
-      if (threadIdx.x == 0) s_skip = uint32_t(t0 - p.off.at(ilo));  // rows of probe row ilo before this tile
+      for (uint32_t r = threadIdx.x; r < ns; r += kThreads) s_beg[r] = d.pbeg[ilo + r];
+      if (threadIdx.x == 0) s_skip = uint32_t(t0 - off_at(d, ilo));  // rows of probe row ilo before this tile
       __syncthreads();
       if (q0 < n) {
-        uint32_t k = upper_bound_u32(s_rel, 0, ns + 1, q0) - 1;
+        uint32_t r = upper_bound_u32(s_rel, 0, ns + 1, q0) - 1;
         const uint32_t skip = s_skip;
 #pragma unroll 4
         for (int j = 0; j < kWriteRows; ++j) {
           const uint32_t q = q0 + j;
           if (q >= n) break;
-          if (s_rel[k + 1] <= q) {
-            ++k;
-            if (s_rel[k + 1] <= q) k = upper_bound_u32(s_rel, k + 1, ns + 1, q) - 1;
+          if (s_rel[r + 1] <= q) {
+            ++r;
+            if (s_rel[r + 1] <= q) r = upper_bound_u32(s_rel, r + 1, ns + 1, q) - 1;
           }
-          s_pk[mi(q)] = k;
-          s_bk[mi(q)] = s_beg[k] + (q - s_rel[k]) + (k == 0 ? skip : 0u);
+          s_pk[mi(q)] = r;
+          s_bk[mi(q)] = s_beg[r] + (q - s_rel[r]) + (r == 0 ? skip : 0u);
         }
       }
     } else if (q0 < n) {
       // more probe rows than the stage holds (rows with few matches): global search
       const uint64_t hi = ilo + nst + 1;
-      uint64_t i = p.off.row_of(t0 + q0, ilo, hi);
+      uint64_t i = row_of(d, t0 + q0, ilo, hi);
       for (int j = 0; j < kWriteRows; ++j) {
         const uint32_t q = q0 + j;
         if (q >= n) break;
         const uint64_t r = t0 + q;
-        if (p.off.at(i + 1) <= r) i = p.off.row_of(r, i + 1, hi);
+        if (off_at(d, i + 1) <= r) i = row_of(d, r, i + 1, hi);
         s_pk[mi(q)] = uint32_t(i - ilo);
-        s_bk[mi(q)] = p.pbeg[i] + uint32_t(r - p.off.at(i));
+        s_bk[mi(q)] = d.pbeg[i] + uint32_t(r - off_at(d, i));
       }
     }
     __syncthreads();
-    uint32_t pk[kWriteRows], bk[kWriteRows];
-#pragma unroll
-    for (int j = 0; j < kWriteRows; ++j) {
-      const uint32_t q = uint32_t(j) * kThreads + threadIdx.x;
-      pk[j] = q < n ? s_pk[mi(q)] : 0u;
-      bk[j] = q < n ? s_bk[mi(q)] : 0u;
-    }
-    for (int c = 0; c < p.ncols; ++c) {
-      const bool fb = (p.from_build >> c) & 1u;
-      const uint32_t* src = fb ? p.src[c] : p.src[c] + ilo;
-      const uint32_t st = fb ? p.bstride : 1u;
-      uint32_t* dst = p.out[c] + t0;
-      uint32_t x[kWriteRows];
+    // probe-side columns, then build-side columns: one index array live at a time
+    for (int side = 0; side < 2; ++side) {
+      const uint32_t* s_map = side ? s_bk : s_pk;
+      uint32_t idx[kWriteRows];
 #pragma unroll
       for (int j = 0; j < kWriteRows; ++j) {
         const uint32_t q = uint32_t(j) * kThreads + threadIdx.x;
-        x[j] = q < n ? __ldg(src + uint64_t(fb ? bk[j] : pk[j]) * st) : 0u;
+        idx[j] = q < n ? s_map[mi(q)] : 0u;
       }
-#pragma unroll
-      for (int j = 0; j < kWriteRows; ++j) {
-        const uint32_t q = uint32_t(j) * kThreads + threadIdx.x;
-        if (q < n) __stcs(dst + q, x[j]);
+      const uint32_t st = side ? uint32_t(d.nbv) : 1u;
+      for (int c = 0; c < d.ncols; ++c) {
+        if (int((d.from_build >> c) & 1u) != side) continue;
+        const uint32_t* src = side ? d.src[c] : d.src[c] + ilo;
+        if (n == kWriteTile) write_column<true>(src, idx, st, d.out[c] + t0, n);
+        else write_column<false>(src, idx, st, d.out[c] + t0, n);
       }
     }
     __syncthreads();
   }
 }
 
-struct CrossParams {
-  uint64_t np, nb, T;
-  const uint32_t* src[MAPSQ_MAX_VARS];
-  uint32_t* out[MAPSQ_MAX_VARS];
-  uint32_t from_build;   // bit c: column c comes from the smaller table
-  int ncols;
-};
-
-// Cross product (no shared variable): output row r pairs probe row r / nb with
-// build row r % nb.
-__global__ void __launch_bounds__(kThreads) cross_write_kernel(CrossParams p) {
-  const uint64_t ngroups = (p.T + 3) / 4;
-  for (uint64_t g = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += uint64_t(gridDim.x) * blockDim.x) {
-    const uint64_t r0 = 4 * g;
-    const int nr = int(min(uint64_t(4), p.T - r0));
-    uint64_t pi[4], bi[4];
-    uint64_t i = r0 / p.nb, j = r0 - i * p.nb;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      pi[k] = i;
-      bi[k] = j;
-      if (++j == p.nb) { j = 0; ++i; }
-    }
-    for (int c = 0; c < p.ncols; ++c) {
-      const bool fb = (p.from_build >> c) & 1u;
-      uint32_t v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) v[k] = k < nr ? __ldg(p.src[c] + (fb ? bi[k] : pi[k])) : 0u;
-      if (nr == 4) {
-        __stcs(reinterpret_cast<uint4*>(p.out[c] + r0), make_uint4(v[0], v[1], v[2], v[3]));
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (k < nr) __stcs(p.out[c] + r0 + k, v[k]);
-      }
+// Cross products (no shared variable): output row r pairs probe row r / nb
+// with build row r % nb; items are output tiles of kWriteTile rows.
+__global__ void __launch_bounds__(kThreads) cross_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                              uint32_t k) {
+  const uint32_t jj = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[jj];
+  const uint64_t t0 = (blockIdx.x - first[jj]) * kWriteTile;
+  const uint64_t n = min(uint64_t(kWriteTile), d.T - t0);
+  for (uint64_t q = threadIdx.x; q < n; q += kThreads) {
+    const uint64_t r = t0 + q;
+    const uint64_t i = r / d.nb, b = r - i * d.nb;
+    for (int c = 0; c < d.ncols; ++c) {
+      const bool fb = (d.from_build >> c) & 1u;
+      __stcs(d.out[c] + r, __ldg(d.src[c] + (fb ? b : i)));
     }
   }
-}
-
-unsigned grid_for(uint64_t n, uint64_t cap = 152ull * 16) {
-  return unsigned(std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(n, 256), cap)));
 }
 
 struct Layout {
@@ -631,12 +664,12 @@ int make_layout(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, Layout* la
     return -1;
   };
   int n = 0;
-  for (int k = 0; k < ns; ++k) {
-    lay->lkey[k] = find(L, shared[k]);
-    lay->rkey[k] = find(R, shared[k]);
-    lay->var[n] = shared[k];
+  for (int q = 0; q < ns; ++q) {
+    lay->lkey[q] = find(L, shared[q]);
+    lay->rkey[q] = find(R, shared[q]);
+    lay->var[n] = shared[q];
     lay->side[n] = 0;
-    lay->col[n] = lay->lkey[k];
+    lay->col[n] = lay->lkey[q];
     ++n;
   }
   auto is_shared = [&](int32_t v) { return std::find(shared, shared + ns, v) != shared + ns; };
@@ -659,41 +692,42 @@ int check_table(Ctx* ctx, const mapsq_table* t, const char* which) {
       return set_error(ctx, MAPSQ_ERR_INVALID, "%s table: variable id %d", which, t->var[c]);
     if (seen & (1u << t->var[c])) return set_error(ctx, MAPSQ_ERR_INVALID, "%s table: variable %d twice", which, t->var[c]);
     seen |= 1u << t->var[c];
-    if (t->nrows && (!t->col[c] || (reinterpret_cast<uintptr_t>(t->col[c]) & 15)))
-      return set_error(ctx, MAPSQ_ERR_INVALID, "%s table: column %u is NULL or not 16-byte aligned", which, c);
+    if (t->nrows && (!t->col[c] || (reinterpret_cast<uintptr_t>(t->col[c]) & 3)))
+      return set_error(ctx, MAPSQ_ERR_INVALID, "%s table: column %u is NULL or not 4-byte aligned", which, c);
   }
   if (t->ncols && t->nrows && !t->on_device)
     return set_error(ctx, MAPSQ_ERR_INVALID, "%s table: columns must be on the device", which);
   return MAPSQ_OK;
 }
 
-// One join, split in two halves so that the caller can allocate the output once
-// its size is known: count() runs the map, shuffle and count passes and sets T;
-// write() runs the partition and write passes.  Device memory comes from
-// ``Mem`` (the context's allocator, or a fixed array carved by the caller), and
-// ``host`` is a host buffer of at least kHllRegs / 2 + 2 words for read-backs.
+// Host side of one join of a batch.
+struct JoinPlan {
+  Layout lay;
+  const mapsq_table *B = nullptr, *P = nullptr;
+  int bside = 1;
+  const int *bkey = nullptr, *pkey = nullptr;
+  uint64_t nb = 0, np = 0, T = 0, M = 0;
+  bool cross = false, hash = false, hll = false;
+};
+
+// A batch of k joins, split in two halves so that the caller can allocate the
+// outputs once their sizes are known: count() runs the map, shuffle and count
+// phases and sets every T; write() runs the partition and write phases.
+// Device memory comes from ``Mem`` (the context's allocator, or a fixed array
+// carved by the caller).
 template <class Mem>
-struct HashJoin {
-  Ctx* ctx;               // NULL without a context (no profiling, no launch count)
+struct BatchJoin {
+  Ctx* ctx;               // NULL without a context (no profiling, no launch count, pageable copies)
   cudaStream_t stream;
   uint32_t* status;       // device status word
   Mem* mem;
-  uint64_t* host;
-  Layout lay;
-  const mapsq_table *L = nullptr, *R = nullptr, *B = nullptr, *P = nullptr;
-  int bside = 1;
-  const int *bkey = nullptr, *pkey = nullptr;
-  uint64_t nb = 0, np = 0, T = 0;
-  bool cross = false, off32 = true;
-  KeyCols bk{}, pk{};
-  HashTable table{};
-  uint64_t M = 0;
-  uint32_t* grouped = nullptr;
-  uint32_t nbv = 0;       // build value columns (row-major stride of ``grouped``)
-  uint64_t nt = 0;                 // count tiles
-  void* local = nullptr;           // tile-local output offsets of the probe rows (u32 or u64)
-  uint32_t* pbeg = nullptr;        // group start of each probe row
-  uint64_t* tile_base = nullptr;   // nt + 1
+  std::vector<JoinPlan> plans;
+  std::vector<JoinDesc> descs;
+  JoinDesc* d_descs = nullptr;
+  uint64_t* d_first = nullptr;             // kPhases x (k + 1) item offsets
+  std::vector<uint64_t> first;             // host copy
+  std::vector<uint64_t> host;              // read-back buffer
+  uint32_t k = 0;
 
   int fail(int code, const char* what) { return ctx ? set_error(ctx, code, "%s", what) : code; }
   int cuda(cudaError_t e, const char* what) {
@@ -706,238 +740,337 @@ struct HashJoin {
   void done(int r, double bytes) {
     if (ctx) prof_end(ctx, r, bytes);
   }
+  int upload(void* dst, const void* src, size_t bytes) {
+    if (ctx) return stage_upload(ctx, dst, src, bytes);
+    MQ_TRY(cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "upload"));
+    return cuda(cudaStreamSynchronize(stream), "upload");  // pageable source: wait before it goes away
+  }
+  // Reads ``words`` 64-bit words, then the status word into host[words].
+  int readback(const void* dptr, size_t words) {
+    host.assign(words + 1, 0);
+    MQ_TRY(cuda(cudaMemcpyAsync(host.data(), dptr, words * 8, cudaMemcpyDeviceToHost, stream), "readback"));
+    MQ_TRY(cuda(cudaMemcpyAsync(host.data() + words, status, 4, cudaMemcpyDeviceToHost, stream), "status"));
+    return cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  }
+  uint64_t* phase_first(int ph) { return d_first + size_t(ph) * (k + 1); }
+  uint64_t items(int ph) const { return first[size_t(ph) * (k + 1) + k]; }
+  // item offsets of phase ph from per-join item counts
+  void set_items(int ph, const std::vector<uint64_t>& per) {
+    uint64_t* f = first.data() + size_t(ph) * (k + 1);
+    f[0] = 0;
+    for (uint32_t j = 0; j < k; ++j) f[j + 1] = f[j] + per[j];
+  }
 
-  int prepare(const mapsq_table* left, const mapsq_table* right) {
-    L = left;
-    R = right;
-    MQ_TRY(check_table(ctx, L, "left"));
-    MQ_TRY(check_table(ctx, R, "right"));
-    MQ_TRY(make_layout(ctx, L, R, &lay));
-    const bool build_left = L->nrows < R->nrows;  // build on the smaller side
-    B = build_left ? L : R;
-    P = build_left ? R : L;
-    bside = build_left ? 0 : 1;
-    bkey = build_left ? lay.lkey : lay.rkey;
-    pkey = build_left ? lay.rkey : lay.lkey;
-    nb = B->nrows;
-    np = P->nrows;
-    cross = lay.nkey == 0;
-    if (nb >= (uint64_t(1) << 31)) return fail(MAPSQ_ERR_UNSUPPORTED, "build side of 2^31 rows or more");
-    if (!cross) {
-      bk = KeyCols{B->col[bkey[0]], lay.nkey == 2 ? B->col[bkey[1]] : nullptr};
-      pk = KeyCols{P->col[pkey[0]], lay.nkey == 2 ? P->col[pkey[1]] : nullptr};
+  int prepare(uint32_t nj, const mapsq_table* const* L, const mapsq_table* const* R) {
+    k = nj;
+    plans.assign(k, JoinPlan{});
+    descs.assign(k, JoinDesc{});
+    first.assign(size_t(kPhases) * (k + 1), 0);
+    for (uint32_t j = 0; j < k; ++j) {
+      JoinPlan& pl = plans[j];
+      if (!L[j] || !R[j]) return fail(MAPSQ_ERR_INVALID, "NULL table in a join batch");
+      MQ_TRY(check_table(ctx, L[j], "left"));
+      MQ_TRY(check_table(ctx, R[j], "right"));
+      MQ_TRY(make_layout(ctx, L[j], R[j], &pl.lay));
+      const bool build_left = L[j]->nrows < R[j]->nrows;  // build on the smaller side
+      pl.B = build_left ? L[j] : R[j];
+      pl.P = build_left ? R[j] : L[j];
+      pl.bside = build_left ? 0 : 1;
+      pl.bkey = build_left ? pl.lay.lkey : pl.lay.rkey;
+      pl.pkey = build_left ? pl.lay.rkey : pl.lay.lkey;
+      pl.nb = pl.B->nrows;
+      pl.np = pl.P->nrows;
+      pl.cross = pl.lay.nkey == 0;
+      pl.hash = !pl.cross && pl.nb > 0 && pl.np > 0;
+      pl.hll = pl.hash && pl.nb >= kHllMinBuild;
+      if (pl.nb >= (uint64_t(1) << 31)) return fail(MAPSQ_ERR_UNSUPPORTED, "build side of 2^31 rows or more");
+      if (pl.cross && pl.nb && pl.np > UINT64_MAX / pl.nb) return fail(MAPSQ_ERR_BUDGET, "cross product overflows 64 bits");
+      JoinDesc& d = descs[j];
+      d.nb = pl.nb;
+      d.np = pl.np;
+      d.cross = pl.cross;
+      d.hash = pl.hash;
+      if (!pl.cross) {
+        d.bk = KeyCols{pl.B->col[pl.bkey[0]], pl.lay.nkey == 2 ? pl.B->col[pl.bkey[1]] : nullptr};
+        d.pk = KeyCols{pl.P->col[pl.pkey[0]], pl.lay.nkey == 2 ? pl.P->col[pl.pkey[1]] : nullptr};
+      }
+      for (int c = pl.lay.nkey; c < pl.lay.ncols; ++c)
+        if (pl.lay.side[c] == pl.bside) d.bsrc[d.nbv++] = pl.B->col[pl.lay.col[c]];
     }
     return MAPSQ_OK;
   }
 
-  // Reads ``count`` 64-bit words and then the status word, synchronising the stream.
-  int readback(const void* dptr, int count) {
-    host[count] = 0;  // the status word fills only its low half
-    MQ_TRY(cuda(cudaMemcpyAsync(host, dptr, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost, stream), "readback"));
-    MQ_TRY(cuda(cudaMemcpyAsync(host + count, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream), "status"));
-    MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
-    return MAPSQ_OK;
-  }
-
-  int build_table() {
-    uint32_t *slot_of = nullptr, *rank_of = nullptr;
-    uint64_t* lb = nullptr;
-    MQ_TRY(mem->get(M, &table.keys));
-    MQ_TRY(mem->get(M + 1, &table.group));
-    table.M = uint32_t(M);
-    MQ_TRY(mem->get(nb, &slot_of));
-    MQ_TRY(mem->get(nb, &rank_of));
-    MQ_TRY(mem->get(lookback_scratch_words(M + 1), &lb));
-    MQ_TRY(cuda(cudaMemsetAsync(lb, 0, lookback_scratch_words(M + 1) * sizeof(uint64_t), stream), "memset"));
-    MQ_TRY(cuda(cudaMemsetAsync(table.keys, 0xff, M * sizeof(uint64_t), stream), "memset"));  // all empty
-    MQ_TRY(cuda(cudaMemsetAsync(table.group, 0, (M + 1) * sizeof(uint2), stream), "memset"));
-    int r = rec(K_HASH_INSERT);
-    hash_insert_kernel<<<grid_for(nb, 152ull * 32), 256, 0, stream>>>(bk, nb, table, slot_of, rank_of, status);
-    launched();
-    done(r, 4.0 * lay.nkey * nb);
-    r = rec(K_PREFIX_SUM);
-    slot_prefix_kernel<<<unsigned(ceil_div(M + 1, kLbTile)), kLbThreads, 0, stream>>>(table.group, M + 1, lb, status);
-    launched();
-    done(r, 8.0 * (M + 1));
-    BuildValues bv{};
-    for (int c = lay.nkey; c < lay.ncols; ++c)
-      if (lay.side[c] == bside) bv.src[bv.n++] = B->col[lay.col[c]];
-    nbv = uint32_t(bv.n);
-    if (nbv) {
-      MQ_TRY(mem->get(nb * nbv, &grouped));
-      r = rec(K_HASH_SCATTER);
-      hash_scatter_kernel<<<grid_for(ceil_div(nb, kScatterRows), 152ull * 16), 256, 0, stream>>>(
-          bv, nb, slot_of, rank_of, table.group, grouped);
+  // Distinct-key estimates of the large build sides, then the table sizes.
+  int size_tables() {
+    std::vector<uint64_t> per(k, 0);
+    uint32_t nh = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+      const JoinPlan& pl = plans[j];
+      plans[j].M = pl.hash ? std::max<uint64_t>(1024, 2 * pl.nb) : 0;
+      if (pl.hll) {
+        per[j] = ceil_div(pl.nb, kRowTile);
+        ++nh;
+      }
+    }
+    if (nh) {
+      uint32_t* regs = nullptr;
+      MQ_TRY(mem->get(size_t(nh) * kHllRegs, &regs));
+      MQ_TRY(cuda(cudaMemsetAsync(regs, 0, size_t(nh) * kHllRegs * 4, stream), "memset"));
+      uint32_t h = 0;
+      for (uint32_t j = 0; j < k; ++j)
+        if (plans[j].hll) descs[j].hll = regs + size_t(h++) * kHllRegs;
+      set_items(PH_HLL, per);
+      MQ_TRY(upload_descs());
+      int r = rec(K_HLL);
+      hll_kernel<<<unsigned(items(PH_HLL)), kThreads, 0, stream>>>(d_descs, phase_first(PH_HLL), k);
       launched();
-      done(r, 4.0 * nbv * nb);
+      double bytes = 0;
+      for (auto& pl : plans) bytes += pl.hll ? 4.0 * pl.lay.nkey * pl.nb : 0;
+      done(r, bytes);
+      MQ_TRY(cuda(cudaGetLastError(), "hll_kernel"));
+      MQ_TRY(readback(regs, size_t(nh) * kHllRegs / 2));
+      h = 0;
+      for (uint32_t j = 0; j < k; ++j) {
+        if (!plans[j].hll) continue;
+        const double est = hll_estimate(reinterpret_cast<const uint32_t*>(host.data()) + size_t(h++) * kHllRegs);
+        // load factor about 0.6
+        plans[j].M = std::min<uint64_t>(plans[j].M, std::max<uint64_t>(1024, uint64_t(1.6 * est) + 1024));
+      }
     }
-    return cuda(cudaGetLastError(), "hash build kernels");
+    for (auto& pl : plans) {
+      if (pl.M >= 0xfffffff0ull) pl.M = 0xfffffff0ull;
+      pl.M = (pl.M + kBucket - 1) / kBucket * kBucket;
+    }
+    return MAPSQ_OK;
   }
 
-  template <class OffT>
-  int probe() {
-    OffT* loc = nullptr;
-    uint64_t* tot = nullptr;
-    nt = ceil_div(np, kProbeTile);
-    MQ_TRY(mem->get(np, &loc));
-    if (!pbeg) MQ_TRY(mem->get(np, &pbeg));
-    MQ_TRY(mem->get(nt, &tot));
-    MQ_TRY(mem->get(nt + 1, &tile_base));
-    int r = rec(K_PROBE_COUNT);
-    probe_count_kernel<OffT><<<unsigned(nt), kThreads, 0, stream>>>(pk, np, table, loc, pbeg, tot, status);
+  // Descriptors and item offsets go up together, in one copy.
+  int upload_descs() {
+    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size();
+    if (!d_descs) {
+      unsigned char* blob = nullptr;
+      MQ_TRY(mem->get(db + fb, &blob));
+      d_descs = reinterpret_cast<JoinDesc*>(blob);
+      d_first = reinterpret_cast<uint64_t*>(blob + db);
+    }
+    blob_host.resize(db + fb);
+    memcpy(blob_host.data(), descs.data(), db);
+    memcpy(blob_host.data() + db, first.data(), fb);
+    return upload(d_descs, blob_host.data(), db + fb);
+  }
+  std::vector<unsigned char> blob_host;
+
+  // Tables and per-join scratch; item offsets of the build and count phases.
+  int allocate() {
+    size_t keys = 0, groups = 0;
+    for (auto& pl : plans)
+      if (pl.hash) {
+        keys += pl.M;
+        groups += pl.M + 1;
+      }
+    uint64_t *all_keys = nullptr;
+    uint2* all_groups = nullptr;
+    MQ_TRY(mem->get(std::max<size_t>(keys, 1), &all_keys));
+    MQ_TRY(mem->get(std::max<size_t>(groups, 1), &all_groups));
+    if (keys) MQ_TRY(cuda(cudaMemsetAsync(all_keys, 0xff, keys * 8, stream), "memset"));  // all slots empty
+    if (groups) MQ_TRY(cuda(cudaMemsetAsync(all_groups, 0, groups * 8, stream), "memset"));
+    std::vector<uint64_t> ins(k, 0), slots(k, 0), scat(k, 0), cnt(k, 0);
+    size_t ko = 0, go = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+      const JoinPlan& pl = plans[j];
+      JoinDesc& d = descs[j];
+      if (!pl.hash) continue;
+      d.t.keys = all_keys + ko;
+      d.t.group = all_groups + go;
+      d.t.M = uint32_t(pl.M);
+      ko += pl.M;
+      go += pl.M + 1;
+      const uint64_t nslot_tiles = ceil_div(pl.M + 1, kRowTile);
+      const uint64_t nt = ceil_div(pl.np, kRowTile);
+      MQ_TRY(mem->get(nslot_tiles, &d.slot_total));
+      MQ_TRY(mem->get(nslot_tiles + 1, &d.t.slot_base));
+      MQ_TRY(mem->get(pl.nb, &d.slot_of));
+      MQ_TRY(mem->get(pl.nb, &d.rank_of));
+      if (d.nbv) MQ_TRY(mem->get(pl.nb * d.nbv, &d.grouped));
+      MQ_TRY(mem->get(pl.np, &d.local));
+      MQ_TRY(mem->get(pl.np, &d.pbeg));
+      MQ_TRY(mem->get(nt, &d.tile_total));
+      MQ_TRY(mem->get(nt + 1, &d.tile_base));
+      ins[j] = ceil_div(pl.nb, kRowTile);
+      slots[j] = nslot_tiles;
+      scat[j] = d.nbv ? ins[j] : 0;
+      cnt[j] = nt;
+    }
+    set_items(PH_INSERT, ins);
+    set_items(PH_SLOTS, slots);
+    set_items(PH_SCATTER, scat);
+    set_items(PH_COUNT, cnt);
+    return MAPSQ_OK;
+  }
+
+  int count_phases(uint64_t* totals) {
+    MQ_TRY(upload_descs());
+    double bytes = 0;
+    int r = rec(K_HASH_INSERT);
+    if (items(PH_INSERT)) {
+      hash_insert_kernel<<<unsigned(items(PH_INSERT)), kThreads, 0, stream>>>(d_descs, phase_first(PH_INSERT), k,
+                                                                               status);
+      launched();
+    }
+    for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.nb : 0;
+    done(r, bytes);
+    r = rec(K_PREFIX_SUM);
+    if (items(PH_SLOTS)) {
+      slot_scan_kernel<<<unsigned(items(PH_SLOTS)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SLOTS), k);
+      launched();
+      tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 0, nullptr);
+      launched();
+    }
+    bytes = 0;
+    for (auto& pl : plans) bytes += pl.hash ? 16.0 * (pl.M + 1) : 0;
+    done(r, bytes);
+    r = rec(K_HASH_SCATTER);
+    if (items(PH_SCATTER)) {
+      hash_scatter_kernel<<<unsigned(items(PH_SCATTER)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SCATTER), k);
+      launched();
+    }
+    bytes = 0;
+    for (uint32_t j = 0; j < k; ++j) bytes += plans[j].hash ? 4.0 * descs[j].nbv * plans[j].nb : 0;
+    done(r, bytes);
+    r = rec(K_PROBE_COUNT);
+    if (items(PH_COUNT)) {
+      probe_count_kernel<<<unsigned(items(PH_COUNT)), kThreads, 0, stream>>>(d_descs, phase_first(PH_COUNT), k,
+                                                                             status);
+      launched();
+    }
+    bytes = 0;
+    for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.np : 0;
+    done(r, bytes);
+    tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 1, totals);
     launched();
-    done(r, 4.0 * lay.nkey * np);
-    tile_scan_kernel<<<1, 1024, 0, stream>>>(tot, nt, tile_base);
-    launched();
-    local = loc;
-    return cuda(cudaGetLastError(), "probe_count_kernel");
+    return cuda(cudaGetLastError(), "count phases");
   }
 
   int count() {
-    T = 0;
-    if (nb == 0 || np == 0) return MAPSQ_OK;
-    if (cross) {
-      if (np > UINT64_MAX / nb) return fail(MAPSQ_ERR_BUDGET, "cross product overflows 64 bits");
-      T = np * nb;
-      return MAPSQ_OK;
-    }
     MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
-    M = std::max<uint64_t>(1024, 2 * nb);
-    if (nb >= kHllMinBuild) {
-      // size the table from the distinct keys: load factor about 0.6
-      uint32_t* regs = nullptr;
-      MQ_TRY(mem->get(kHllRegs, &regs));
-      MQ_TRY(cuda(cudaMemsetAsync(regs, 0, kHllRegs * sizeof(uint32_t), stream), "memset"));
-      int r = rec(K_HLL);
-      hll_kernel<<<grid_for(nb / 4, 152ull * 8), 256, 0, stream>>>(bk, nb, regs);
-      launched();
-      done(r, 4.0 * lay.nkey * nb);
-      MQ_TRY(readback(regs, kHllRegs / 2));
-      double est = hll_estimate(reinterpret_cast<const uint32_t*>(host));
-      M = std::min<uint64_t>(M, std::max<uint64_t>(1024, uint64_t(1.6 * est) + 1024));
-    }
-    if (M >= 0xfffffff0ull) M = 0xfffffff0ull;
-    M = (M + kBucket - 1) / kBucket * kBucket;
+    MQ_TRY(size_tables());
+    uint64_t* totals = nullptr;
+    MQ_TRY(mem->get(k, &totals));
     for (int attempt = 0;; ++attempt) {
-      MQ_TRY(build_table());
-      if (off32) {
-        MQ_TRY(probe<uint32_t>());
-      } else {
-        MQ_TRY(probe<uint64_t>());
-      }
-      MQ_TRY(readback(tile_base + nt, 1));
-      const uint32_t st = uint32_t(host[1]);
+      MQ_TRY(allocate());
+      MQ_TRY(count_phases(totals));
+      MQ_TRY(readback(totals, k));
+      const uint32_t st = uint32_t(host[k]);
       if (st & 1u) {
-        // a distinct-key estimate far too low: rebuild at two slots per build row
-        if (attempt > 0 || M >= 2 * nb) return fail(MAPSQ_ERR_CUDA, "hash table full");
-        M = (std::max<uint64_t>(1024, 2 * nb) + kBucket - 1) / kBucket * kBucket;
+        // a distinct-key estimate far too low: rebuild every table at two slots per build row
+        if (attempt > 0) return fail(MAPSQ_ERR_CUDA, "hash table full");
+        for (auto& pl : plans)
+          if (pl.hash) pl.M = (std::max<uint64_t>(1024, 2 * pl.nb) + kBucket - 1) / kBucket * kBucket;
         MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
         continue;
       }
-      if (st & 2u) return fail(MAPSQ_ERR_TIMEOUT, "a prefix-sum look-back wait gave up");
-      if (st & 4u) {
-        // a count tile's total needs 64-bit local offsets: count again with them
-        if (!off32) return fail(MAPSQ_ERR_CUDA, "device status word set");
-        off32 = false;
-        MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
-        MQ_TRY(probe<uint64_t>());
-        MQ_TRY(readback(tile_base + nt, 1));
-        if (host[1]) return fail(MAPSQ_ERR_CUDA, "device status word set");
-      } else if (st) {
-        return fail(MAPSQ_ERR_CUDA, "device status word set");
-      }
-      T = host[0];
+      if (st & 4u)
+        return fail(MAPSQ_ERR_UNSUPPORTED, "2048 consecutive probe rows with 2^32 or more matches");
+      if (st) return fail(MAPSQ_ERR_CUDA, "device status word set");
+      for (uint32_t j = 0; j < k; ++j) plans[j].T = descs[j].T = host[j];
       return MAPSQ_OK;
     }
   }
 
-  template <class OffT>
-  int write_hash(uint32_t* const* out_cols) {
-    WriteParams<OffT> wp{};
-    wp.off = Offsets<OffT>{static_cast<const OffT*>(local), tile_base, np, T};
-    wp.pbeg = pbeg;
-    wp.np = np;
-    wp.nb = nb;
-    wp.T = T;
-    wp.ncols = lay.ncols;
-    wp.bstride = nbv;
-    const uint64_t ntiles = ceil_div(T, kWriteTile);
-    uint64_t* part = nullptr;
-    MQ_TRY(mem->get(ntiles + 1, &part));
-    int r = rec(K_PARTITION);
-    write_partition_kernel<OffT><<<grid_for(ntiles + 1, 152ull * 8), 256, 0, stream>>>(wp.off, nt, ntiles, part);
-    launched();
-    done(r, 8.0 * (ntiles + 1));
-    wp.part = part;
-    double in_bytes = 0;
-    uint32_t j = 0;
-    for (int c = 0; c < lay.ncols; ++c) {
-      const bool fb = lay.side[c] == bside && c >= lay.nkey;
-      wp.out[c] = out_cols[c];
-      if (fb) {
-        wp.src[c] = grouped + j++;
-        wp.from_build |= 1u << c;
-        in_bytes += 4.0 * nb;
+  // Partition and write phases into out[j] (ncols device columns of T rows each).
+  int write(uint32_t* const* const* out) {
+    std::vector<uint64_t> part(k, 0), wr(k, 0), cr(k, 0);
+    double bytes = 0, cbytes = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+      const JoinPlan& pl = plans[j];
+      JoinDesc& d = descs[j];
+      d.ncols = pl.lay.ncols;
+      d.from_build = 0;
+      uint32_t b = 0;
+      double in = 0;
+      for (int c = 0; c < pl.lay.ncols; ++c) {
+        const bool fb = pl.lay.side[c] == pl.bside && c >= pl.lay.nkey;
+        d.out[c] = out[j][c];
+        if (fb) {
+          d.src[c] = pl.cross ? pl.B->col[pl.lay.col[c]] : d.grouped + b++;
+          d.from_build |= 1u << c;
+          in += 4.0 * pl.nb;
+        } else {
+          // key columns and the probe side's own columns come from the probe row
+          d.src[c] = pl.P->col[c < pl.lay.nkey ? pl.pkey[c] : pl.lay.col[c]];
+          if (c >= pl.lay.nkey) in += 4.0 * pl.np;
+        }
+      }
+      if (!pl.T || !pl.lay.ncols) continue;
+      const uint64_t ntiles = ceil_div(pl.T, kWriteTile);
+      if (pl.cross) {
+        cr[j] = ntiles;
+        cbytes += 4.0 * pl.T * pl.lay.ncols + in;
       } else {
-        // key columns and the probe side's own columns come from the probe row
-        wp.src[c] = P->col[c < lay.nkey ? pkey[c] : lay.col[c]];
-        if (c >= lay.nkey) in_bytes += 4.0 * np;
+        MQ_TRY(mem->get(ntiles + 1, &d.part));
+        part[j] = ceil_div(ntiles + 1, kThreads);
+        wr[j] = ntiles;
+        bytes += 4.0 * pl.T * pl.lay.ncols + in;
       }
     }
-    unsigned grid = unsigned(std::min<uint64_t>(ntiles, 152ull * 8));
-    r = rec(K_JOIN_WRITE);
-    join_write_kernel<OffT><<<grid, kThreads, 0, stream>>>(wp);
-    launched();
-    done(r, 4.0 * double(T) * lay.ncols + in_bytes);
-    return cuda(cudaGetLastError(), "join_write_kernel");
-  }
-
-  int write_cross(uint32_t* const* out_cols) {
-    CrossParams cp{};
-    cp.np = np;
-    cp.nb = nb;
-    cp.T = T;
-    cp.ncols = lay.ncols;
-    double in_bytes = 0;
-    for (int c = 0; c < lay.ncols; ++c) {
-      const bool fb = lay.side[c] == bside;
-      cp.out[c] = out_cols[c];
-      cp.src[c] = (fb ? B : P)->col[lay.col[c]];
-      if (fb) cp.from_build |= 1u << c;
-      in_bytes += 4.0 * (fb ? nb : np);
+    set_items(PH_PART, part);
+    set_items(PH_WRITE, wr);
+    set_items(PH_CROSS, cr);
+    if (!items(PH_WRITE) && !items(PH_CROSS)) return MAPSQ_OK;
+    MQ_TRY(upload_descs());
+    if (items(PH_WRITE)) {
+      unsigned long long* queue = nullptr;
+      MQ_TRY(mem->get(1, &queue));
+      MQ_TRY(cuda(cudaMemsetAsync(queue, 0, 8, stream), "memset"));
+      int r = rec(K_PARTITION);
+      write_partition_kernel<<<unsigned(items(PH_PART)), kThreads, 0, stream>>>(d_descs, phase_first(PH_PART), k);
+      launched();
+      done(r, 8.0 * items(PH_WRITE));
+      r = rec(K_JOIN_WRITE);
+      const unsigned grid = unsigned(std::min<uint64_t>(items(PH_WRITE), 152ull * 4));
+      join_write_kernel<<<grid, kThreads, 0, stream>>>(d_descs, phase_first(PH_WRITE), k, queue);
+      launched();
+      done(r, bytes);
     }
-    int r = rec(K_CROSS_WRITE);
-    cross_write_kernel<<<grid_for(ceil_div(T, 4), 152ull * 8), kThreads, 0, stream>>>(cp);
-    launched();
-    done(r, 4.0 * double(T) * lay.ncols + in_bytes);
-    return cuda(cudaGetLastError(), "cross_write_kernel");
-  }
-
-  int write(uint32_t* const* out_cols) {
-    if (T == 0 || lay.ncols == 0) return MAPSQ_OK;
-    if (cross) return write_cross(out_cols);
-    return off32 ? write_hash<uint32_t>(out_cols) : write_hash<uint64_t>(out_cols);
+    if (items(PH_CROSS)) {
+      int r = rec(K_CROSS_WRITE);
+      cross_write_kernel<<<unsigned(items(PH_CROSS)), kThreads, 0, stream>>>(d_descs, phase_first(PH_CROSS), k);
+      launched();
+      done(r, cbytes);
+    }
+    return cuda(cudaGetLastError(), "write phases");
   }
 };
 
 }  // namespace
 
-int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
-                TableImpl** out) {
+int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
+               const mapsq_join_opts* opts, TableImpl** out) {
   (void)opts;
+  if (k == 0) return MAPSQ_OK;
   Scratch scratch(ctx);
-  HashJoin<Scratch> j{ctx, ctx->stream, ctx->d_status, &scratch, ctx->h_pinned + 64};
-  MQ_TRY(j.prepare(L, R));
-  MQ_TRY(j.count());
-  TableImpl* t = nullptr;
-  MQ_TRY(table_alloc(ctx, j.T, uint32_t(j.lay.ncols), j.lay.var, &t));
-  int rc = j.write(t->pub.col);
+  BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
+  MQ_TRY(bj.prepare(k, L, R));
+  MQ_TRY(bj.count());
+  std::vector<TableImpl*> tabs(k, nullptr);
+  std::vector<uint32_t* const*> cols(k, nullptr);
+  int rc = MAPSQ_OK;
+  for (uint32_t j = 0; j < k && rc == MAPSQ_OK; ++j) {
+    rc = table_alloc(ctx, bj.plans[j].T, uint32_t(bj.plans[j].lay.ncols), bj.plans[j].lay.var, &tabs[j]);
+    if (rc == MAPSQ_OK) cols[j] = tabs[j]->pub.col;
+  }
+  if (rc == MAPSQ_OK) rc = bj.write(cols.data());
   if (rc != MAPSQ_OK) {
-    table_release(ctx, t);
+    for (auto* t : tabs) table_release(ctx, t);
     return rc;
   }
-  *out = t;
+  for (uint32_t j = 0; j < k; ++j) out[j] = tabs[j];
   return MAPSQ_OK;
+}
+
+int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
+                TableImpl** out) {
+  return join_batch(ctx, 1, &L, &R, opts, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1009,22 +1142,23 @@ extern "C" int mapsq_join_noalloc(const mapsq_table* left, const mapsq_table* ri
   Carve carve{base};
   uint32_t* status = nullptr;
   MQ_TRY(carve.get(64, &status));
-  uint64_t host[kHllRegs / 2 + 8];
-  HashJoin<Carve> j{nullptr, static_cast<cudaStream_t>(cuda_stream), status, &carve, host};
-  MQ_TRY(j.prepare(left, right));
-  if (j.nb > kNoAllocMaxBuild || j.np > kNoAllocMaxProbe) return MAPSQ_ERR_INVALID;  // beyond the scratch array
-  const int ncols = j.lay.ncols;
+  BatchJoin<Carve> bj{nullptr, static_cast<cudaStream_t>(cuda_stream), status, &carve};
+  MQ_TRY(bj.prepare(1, &left, &right));
+  const JoinPlan& pl = bj.plans[0];
+  if (pl.nb > kNoAllocMaxBuild || pl.np > kNoAllocMaxProbe) return MAPSQ_ERR_INVALID;  // beyond the scratch array
+  const int ncols = pl.lay.ncols;
   if (ncols && !out_cols) return MAPSQ_ERR_INVALID;
   for (int c = 0; c < ncols; ++c)
     if (!out_cols[c] || (reinterpret_cast<uintptr_t>(out_cols[c]) & 15)) return MAPSQ_ERR_INVALID;
-  MQ_TRY(j.count());
-  *out_rows = j.T;
-  if (j.T > out_capacity_rows) return MAPSQ_ERR_BUDGET;
+  MQ_TRY(bj.count());
+  *out_rows = pl.T;
+  if (pl.T > out_capacity_rows) return MAPSQ_ERR_BUDGET;
   memset(out, 0, sizeof(*out));
-  out->nrows = j.T;
+  out->nrows = pl.T;
   out->ncols = uint32_t(ncols);
   out->on_device = 1;
-  for (int c = 0; c < MAPSQ_MAX_VARS; ++c) out->var[c] = c < ncols ? j.lay.var[c] : -1;
+  for (int c = 0; c < MAPSQ_MAX_VARS; ++c) out->var[c] = c < ncols ? pl.lay.var[c] : -1;
   for (int c = 0; c < ncols; ++c) out->col[c] = out_cols[c];
-  return j.write(out_cols);
+  uint32_t* const* cols[1] = {out_cols};
+  return bj.write(cols);
 }

@@ -39,41 +39,48 @@ struct StoreCols {
   const uint32_t* os_s;
 };
 
-__device__ __forceinline__ uint64_t lower_bound_u32(const uint32_t* a, uint64_t lo, uint64_t hi, uint32_t v) {
-  while (lo < hi) {
-    uint64_t mid = lo + (hi - lo) / 2;
-    if (a[mid] < v) lo = mid + 1; else hi = mid;
+// Warp-cooperative search in the sorted run a[lo, hi): the first index whose
+// value is >= v (upper = false) or > v (upper = true).  Each round the 32
+// lanes test 32 evenly spaced positions, which narrows the range 32-fold: about
+// five dependent loads for ten million rows instead of twenty-four.
+__device__ __forceinline__ uint64_t warp_bound(const uint32_t* a, uint64_t lo, uint64_t hi, uint32_t v, bool upper) {
+  const unsigned lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const uint64_t step = (hi - lo + 31) / 32;
+    const uint64_t pos = lo + lane * step;
+    const bool below = pos < hi && (upper ? a[pos] <= v : a[pos] < v);
+    const int c = __popc(__ballot_sync(0xffffffffu, below));  // the lanes below v form a prefix
+    if (c == 0) return lo;
+    const uint64_t nlo = lo + uint64_t(c - 1) * step + 1;
+    const uint64_t nhi = c < 32 ? min(hi, lo + uint64_t(c) * step) : hi;
+    lo = nlo;
+    hi = nhi;
   }
-  return lo;
+  const uint64_t pos = lo + lane;
+  const bool below = pos < hi && (upper ? a[pos] <= v : a[pos] < v);
+  return lo + __popc(__ballot_sync(0xffffffffu, below));
 }
 
-__device__ __forceinline__ uint64_t upper_bound_u32(const uint32_t* a, uint64_t lo, uint64_t hi, uint32_t v) {
-  while (lo < hi) {
-    uint64_t mid = lo + (hi - lo) / 2;
-    if (a[mid] <= v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
+// One warp per pattern.
 __global__ void scan_ranges_kernel(const RangeQuery* __restrict__ q, uint32_t n, StoreCols st,
                                    uint64_t* __restrict__ out) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const uint32_t i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (i >= n) return;  // whole warps leave together
   RangeQuery r = q[i];
   uint64_t lo = 0, hi = 0;
   switch (r.kind) {
     case KIND_S_BOUND:
-      lo = lower_bound_u32(st.so_s, r.b, r.e, r.v0);
-      hi = upper_bound_u32(st.so_s, lo, r.e, r.v0);
+      lo = warp_bound(st.so_s, r.b, r.e, r.v0, false);
+      hi = warp_bound(st.so_s, lo, r.e, r.v0, true);
       break;
     case KIND_O_BOUND:
-      lo = lower_bound_u32(st.os_o, r.b, r.e, r.v1);
-      hi = upper_bound_u32(st.os_o, lo, r.e, r.v1);
+      lo = warp_bound(st.os_o, r.b, r.e, r.v1, false);
+      hi = warp_bound(st.os_o, lo, r.e, r.v1, true);
       break;
     case KIND_EXIST: {
-      uint64_t a = lower_bound_u32(st.so_s, r.b, r.e, r.v0);
-      uint64_t z = upper_bound_u32(st.so_s, a, r.e, r.v0);
-      uint64_t k = lower_bound_u32(st.so_o, a, z, r.v1);
+      uint64_t a = warp_bound(st.so_s, r.b, r.e, r.v0, false);
+      uint64_t z = warp_bound(st.so_s, a, r.e, r.v0, true);
+      uint64_t k = warp_bound(st.so_o, a, z, r.v1, false);
       lo = k;
       hi = (k < z && st.so_o[k] == r.v1) ? k + 1 : k;
       break;
@@ -86,8 +93,10 @@ __global__ void scan_ranges_kernel(const RangeQuery* __restrict__ q, uint32_t n,
     default:
       break;
   }
-  out[2 * i] = lo;
-  out[2 * i + 1] = hi;
+  if ((threadIdx.x & 31) == 0) {
+    out[2 * i] = lo;
+    out[2 * i + 1] = hi;
+  }
 }
 
 __global__ void same_var_flags_kernel(const uint32_t* __restrict__ s, const uint32_t* __restrict__ o, uint64_t n,
@@ -151,7 +160,7 @@ int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* ou
   MQ_CUDA(cudaMemcpyAsync(dq, q.data(), n * sizeof(RangeQuery), cudaMemcpyHostToDevice, ctx->stream));
   StoreCols sc{st.so_s, st.so_o, st.os_o, st.os_s};
   int rec = prof_begin(ctx, K_SCAN_RANGES);
-  scan_ranges_kernel<<<(n + 127) / 128, 128, 0, ctx->stream>>>(dq, n, sc, dout);
+  scan_ranges_kernel<<<(n + 3) / 4, 128, 0, ctx->stream>>>(dq, n, sc, dout);
   ++ctx->launches;
   prof_end(ctx, rec, double(n) * 32);
   MQ_CUDA(cudaGetLastError());
@@ -182,22 +191,22 @@ int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImp
     case KIND_EXIST:
       MQ_TRY(table_alloc(ctx, rows, 0, vars, &t));
       break;
-    case KIND_S_BOUND:
-      MQ_TRY(table_alloc(ctx, rows, 1, vars, &t));
-      if (copy_u32(ctx, t->pub.col[0], st.so_o + r.lo, rows) != MAPSQ_OK) { table_release(ctx, t); return MAPSQ_ERR_CUDA; }
+    // a run of the store is already the partial-match table: a view, no copy
+    case KIND_S_BOUND: {
+      uint32_t* cols[1] = {st.so_o + r.lo};
+      MQ_TRY(table_view(ctx, rows, 1, vars, cols, st.shared, &t));
       break;
-    case KIND_O_BOUND:
-      MQ_TRY(table_alloc(ctx, rows, 1, vars, &t));
-      if (copy_u32(ctx, t->pub.col[0], st.os_s + r.lo, rows) != MAPSQ_OK) { table_release(ctx, t); return MAPSQ_ERR_CUDA; }
+    }
+    case KIND_O_BOUND: {
+      uint32_t* cols[1] = {st.os_s + r.lo};
+      MQ_TRY(table_view(ctx, rows, 1, vars, cols, st.shared, &t));
       break;
-    case KIND_TWO_VARS:
-      MQ_TRY(table_alloc(ctx, rows, 2, vars, &t));
-      if (copy_u32(ctx, t->pub.col[0], st.so_s + r.lo, rows) != MAPSQ_OK ||
-          copy_u32(ctx, t->pub.col[1], st.so_o + r.lo, rows) != MAPSQ_OK) {
-        table_release(ctx, t);
-        return MAPSQ_ERR_CUDA;
-      }
+    }
+    case KIND_TWO_VARS: {
+      uint32_t* cols[2] = {st.so_s + r.lo, st.so_o + r.lo};
+      MQ_TRY(table_view(ctx, rows, 2, vars, cols, st.shared, &t));
       break;
+    }
     case KIND_SAME_VAR: {
       Scratch scratch(ctx);
       uint32_t* flag = nullptr;

@@ -199,7 +199,7 @@ int radix_sort3(Ctx* ctx, Cols3 a, Cols3 b, uint64_t n, const int* key_cols, int
 
 void store_release(Ctx* ctx) {
   Store& st = ctx->store;
-  if (st.block) dev_free(ctx, st.block, st.bytes);
+  shared_release(ctx, st.shared);  // scan results that alias the store keep it alive
   st = Store{};
 }
 
@@ -288,8 +288,7 @@ int store_build(Ctx* ctx, const uint32_t* s, const uint32_t* p, const uint32_t* 
   void* blk = nullptr;
   MQ_TRY(dev_alloc(ctx, bytes, &blk));
   uint32_t* base = static_cast<uint32_t*>(blk);
-  st.block = blk;
-  st.bytes = bytes;
+  st.shared = new SharedBlock{blk, bytes, 1};
   st.so_s = base;
   st.so_o = base + stride;
   st.os_o = base + 2 * stride;

@@ -74,6 +74,8 @@ _SIGNATURES = {
     "mapsq_scan_pattern": (C.c_int, [_P, C.POINTER(Pattern), C.POINTER(_TP)]),
     "mapsq_join": (C.c_int, [_P, _TP, _TP, C.POINTER(_TP), C.POINTER(JoinOpts)]),
     "mapsq_query": (C.c_int, [_P, C.POINTER(Pattern), C.c_uint32, C.POINTER(_TP)]),
+    "mapsq_join_batch": (C.c_int, [_P, C.c_uint32, C.POINTER(_TP), C.POINTER(_TP), C.POINTER(_TP),
+                                   C.POINTER(JoinOpts)]),
     "mapsq_table_from_columns": (C.c_int, [_P, C.c_uint64, C.c_uint32, C.POINTER(C.c_int32), C.POINTER(_P), C.c_int,
                                            C.POINTER(_TP)]),
     "mapsq_table_to_host": (C.c_int, [_P, _TP, C.POINTER(_P)]),
@@ -83,6 +85,7 @@ _SIGNATURES = {
     "mapsq_set_profiling": (C.c_int, [_P, C.c_int]),
     "mapsq_kernel_stats": (C.c_int, [_P, C.POINTER(KernelStat), C.c_uint32, C.POINTER(C.c_uint32)]),
     "mapsq_reset_stats": (C.c_int, [_P]),
+    "mapsq_profile_only": (C.c_int, [_P, C.c_char_p]),
     "mapsq_launch_count": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
     "mapsq_join_noalloc": (C.c_int, [_TP, _TP, C.POINTER(_P), C.c_uint64, _TP, C.POINTER(C.c_uint64), _P]),
 }
@@ -180,6 +183,15 @@ def mapsq_join(ctx, left, right, opts=None):
     return out
 
 
+def mapsq_join_batch(ctx, lefts, rights, opts=None):
+    k = len(lefts)
+    la = (_TP * max(k, 1))(*lefts)
+    ra = (_TP * max(k, 1))(*rights)
+    outs = (_TP * max(k, 1))()
+    _check(ctx, lib().mapsq_join_batch(ctx, k, la, ra, outs, C.byref(opts) if opts else None))
+    return [outs[j] for j in range(k)]
+
+
 def mapsq_query(ctx, bgp):
     arr = (Pattern * len(bgp))(*[_pattern(tp) for tp in bgp])
     out = _TP()
@@ -238,6 +250,10 @@ def mapsq_kernel_stats(ctx):
 
 def mapsq_reset_stats(ctx):
     _check(ctx, lib().mapsq_reset_stats(ctx))
+
+
+def mapsq_profile_only(ctx, name=None):
+    _check(ctx, lib().mapsq_profile_only(ctx, name.encode() if name else None))
 
 
 def mapsq_launch_count(ctx):
@@ -354,6 +370,10 @@ class Context:
     def join(self, left: TableRef, right: TableRef, opts=None) -> TableRef:
         return TableRef(self, mapsq_join(self.handle, left.ptr, right.ptr, opts))
 
+    def join_batch(self, lefts, rights, opts=None):
+        return [TableRef(self, p) for p in mapsq_join_batch(self.handle, [x.ptr for x in lefts],
+                                                             [x.ptr for x in rights], opts)]
+
     def query(self, bgp) -> TableRef:
         return TableRef(self, mapsq_query(self.handle, bgp))
 
@@ -374,6 +394,9 @@ class Context:
 
     def reset_stats(self):
         mapsq_reset_stats(self.handle)
+
+    def profile_only(self, name=None):
+        mapsq_profile_only(self.handle, name)
 
     def launch_count(self):
         return mapsq_launch_count(self.handle)

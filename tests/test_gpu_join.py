@@ -188,3 +188,26 @@ def test_profiling_reports_kernels(ctx):
     for k in ("hash_insert", "hash_scatter", "probe_count", "prefix_sum", "join_write"):
         assert stats[k]["launches"] >= 1 and stats[k]["device_ms"] > 0
     assert stats["join_write"]["alg_bytes"] > 12 * 30000
+
+
+def test_join_batch_matches_oracle(ctx):
+    """Batched form: uneven joins plus special cases in one batch, each exact."""
+    batch = [(L, R) for L, R, s in gen.uneven_batch(seed=4, n_joins=12, log_lo=6.0, log_hi=14.0)]
+    r = gen.Rng(14)
+    A = gen.Table([0, 1], [r.u32(123), r.u32(123)])
+    batch += [
+        (A, gen.Table([2], [r.u32(77)])),                                   # cross product
+        (A, gen.Table.unit(1)),                                             # unit
+        (A, gen.Table([0, 5], [np.zeros(0, np.uint32)] * 2)),                # empty side
+        gen.skewed_two_key(seed=3, log_a=14, log_b=12, log_keys=10),        # two-variable key
+        (gen.Table([0, 1], [np.full(50, 7, np.uint32), r.u32(50)]),         # one hot key
+         gen.Table([0, 2], [np.full(3000, 7, np.uint32), r.u32(3000)])),
+    ]
+    lefts = [device_table(ctx, L) for L, R in batch]
+    rights = [device_table(ctx, R) for L, R in batch]
+    outs = ctx.join_batch(lefts, rights)
+    assert len(outs) == len(batch)
+    for i, ((L, R), o) in enumerate(zip(batch, outs)):
+        assert_same_multiset(o, oracle.join_mapreduce(L, R), f"batch item {i}")
+        o.free()
+    assert ctx.join_batch([], []) == []

@@ -67,6 +67,22 @@ def test_scan_every_pattern_kind(ctx, small_graph):
         t.free()
 
 
+def test_scan_results_outlive_a_store_reload(ctx, small_graph):
+    """Scan results may alias the store; replacing the store must not change them."""
+    s, p, o = small_graph
+    ctx.load_triples(s, p, o)
+    G = oracle.distinct_triples(s, p, o)
+    pats = [(0, 6, 1, 5), (0, 0, 3, 1), (int(s[7]), int(p[7]), 0, 4)]
+    held = [(tp, ctx.scan_pattern(tp)) for tp in pats]
+    r = gen.Rng(4)
+    ctx.load_triples(r.below(1000, 30).astype(np.uint32), r.below(1000, 3).astype(np.uint32),
+                     r.below(1000, 30).astype(np.uint32))
+    for tp, t in held:
+        assert_same_multiset(t, oracle.scan_pattern(G, tp), f"held scan {tp}")
+        t.free()
+    ctx.load_triples(s, p, o)
+
+
 def test_scan_same_variable_filter(ctx):
     s = np.array([1, 2, 3, 3, 4, 4], np.uint32)
     p = np.array([0, 0, 0, 1, 0, 0], np.uint32)
