@@ -191,6 +191,15 @@ MAPSQ_API int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* co
  * variables in ascending id.  Errors: as mapsq_scan_pattern and mapsq_join. */
 MAPSQ_API int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out);
 
+/* Batched form of mapsq_query: ``nq`` BGPs (bgps[q] with n[q] patterns)
+ * evaluated together.  Their range searches are one launch; at each level,
+ * every query's next join goes into one batched join (mapsq_join_batch), so
+ * the batch synchronises about once per level instead of once per join.
+ * out[q] receives query q's result (columns in ascending variable id).
+ * All or nothing: on error no table is returned.  Errors: as mapsq_query. */
+MAPSQ_API int mapsq_query_batch(mapsq_ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const uint32_t* n,
+                                mapsq_table** out);
+
 /* Copy ``ncols`` columns of ``nrows`` rows (host pointers, or device pointers if
  * ``on_device``) into a new library-owned device table with variables ``var``.
  * ncols == 0 makes a 0-column table of ``nrows`` (0 or 1) empty bindings.

@@ -211,30 +211,6 @@ int check_status(Ctx* ctx) {
   return set_error(ctx, MAPSQ_ERR_CUDA, "device status 0x%x (hash table full or index out of range)", st);
 }
 
-static bool pattern_var(const mapsq_pattern& tp, uint32_t bit, uint32_t* v) {
-  if (!(tp.var_mask & bit)) return false;
-  *v = bit == MAPSQ_VAR_S ? tp.s : bit == MAPSQ_VAR_P ? tp.p : tp.o;
-  return true;
-}
-
-static uint32_t pattern_var_set(const mapsq_pattern& tp) {
-  uint32_t m = 0, v;
-  if (pattern_var(tp, MAPSQ_VAR_S, &v)) m |= 1u << v;
-  if (pattern_var(tp, MAPSQ_VAR_O, &v)) m |= 1u << v;
-  return m;
-}
-
-// Permute the columns of a result so that its variables are in ascending id
-// (a pointer permutation: no data moves).
-static void canonical_columns(mapsq_table* t) {
-  uint32_t n = t->ncols;
-  for (uint32_t i = 1; i < n; ++i)
-    for (uint32_t j = i; j > 0 && t->var[j - 1] > t->var[j]; --j) {
-      std::swap(t->var[j - 1], t->var[j]);
-      std::swap(t->col[j - 1], t->col[j]);
-    }
-}
-
 }  // namespace mapsq
 
 using namespace mapsq;
@@ -384,53 +360,6 @@ int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* left,
   std::vector<TableImpl*> t(k, nullptr);
   MQ_TRY(join_batch(ctx, k, left, right, opts, t.data()));
   for (uint32_t j = 0; j < k; ++j) out[j] = &t[j]->pub;
-  return MAPSQ_OK;
-}
-
-int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out) {
-  if (!ctx || !bgp || !out || n == 0)
-    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument or empty BGP") : MAPSQ_ERR_INVALID;
-  MQ_CUDA(cudaSetDevice(ctx->device));
-  for (uint32_t i = 0; i < n; ++i) MQ_TRY(validate_pattern(ctx, bgp[i]));
-  if (!ctx->store.loaded) return set_error(ctx, MAPSQ_ERR_INVALID, "no triple store loaded");
-  std::vector<PatternRange> ranges(n);
-  MQ_TRY(scan_ranges(ctx, bgp, n, ranges.data()));
-
-  // Greedy order: fewest matches first, then the connected pattern with fewest matches.
-  std::vector<uint32_t> rest(n), order;
-  for (uint32_t i = 0; i < n; ++i) rest[i] = i;
-  auto size_of = [&](uint32_t i) { return ranges[i].hi - ranges[i].lo; };
-  std::stable_sort(rest.begin(), rest.end(), [&](uint32_t a, uint32_t b) { return size_of(a) < size_of(b); });
-  order.push_back(rest.front());
-  rest.erase(rest.begin());
-  uint32_t seen = pattern_var_set(bgp[order[0]]);
-  while (!rest.empty()) {
-    auto it = std::find_if(rest.begin(), rest.end(), [&](uint32_t i) { return (pattern_var_set(bgp[i]) & seen) != 0; });
-    if (it == rest.end()) it = rest.begin();
-    order.push_back(*it);
-    seen |= pattern_var_set(bgp[*it]);
-    rest.erase(it);
-  }
-
-  TableImpl* acc = nullptr;
-  int rc = scan_emit(ctx, bgp[order[0]], ranges[order[0]], &acc);
-  if (rc != MAPSQ_OK) return rc;
-  for (size_t k = 1; k < order.size(); ++k) {
-    TableImpl* part = nullptr;
-    rc = scan_emit(ctx, bgp[order[k]], ranges[order[k]], &part);
-    if (rc != MAPSQ_OK) {
-      table_release(ctx, acc);
-      return rc;
-    }
-    TableImpl* joined = nullptr;
-    rc = join_tables(ctx, &acc->pub, &part->pub, nullptr, &joined);
-    table_release(ctx, part);
-    table_release(ctx, acc);
-    if (rc != MAPSQ_OK) return rc;
-    acc = joined;
-  }
-  canonical_columns(&acc->pub);
-  *out = &acc->pub;
   return MAPSQ_OK;
 }
 

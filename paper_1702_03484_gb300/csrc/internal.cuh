@@ -207,6 +207,10 @@ int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const maps
 int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
                const mapsq_join_opts* opts, TableImpl** out);
 
+// BGP evaluation (query.cu): pattern order, and many BGPs level by level.
+std::vector<uint32_t> plan_order(const mapsq_pattern* bgp, uint32_t n, const PatternRange* ranges);
+int query_batch(Ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const uint32_t* ns, TableImpl** out);
+
 inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
 }  // namespace mapsq

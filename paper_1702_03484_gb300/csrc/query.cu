@@ -1,0 +1,154 @@
+// BGP evaluation, the host side of the paper's CPU/GPU coprocessing split
+// (Section 2): the host orders each BGP's patterns and drives the device's
+// pattern scans and joins, one pattern at a time, joining the partial results
+// after each match.  Many BGPs are evaluated together: their range searches are
+// one launch, and at every level each query's next join goes into one batched
+// join (every phase one launch for all of them).
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mapsq {
+
+namespace {
+
+uint32_t pattern_var_set(const mapsq_pattern& tp) {
+  uint32_t m = 0;
+  if (tp.var_mask & MAPSQ_VAR_S) m |= 1u << tp.s;
+  if (tp.var_mask & MAPSQ_VAR_O) m |= 1u << tp.o;
+  return m;
+}
+
+// Permute the columns of a result so that its variables are in ascending id
+// (a pointer permutation: no data moves).
+void canonical_columns(mapsq_table* t) {
+  const uint32_t n = t->ncols;
+  for (uint32_t i = 1; i < n; ++i)
+    for (uint32_t j = i; j > 0 && t->var[j - 1] > t->var[j]; --j) {
+      std::swap(t->var[j - 1], t->var[j]);
+      std::swap(t->col[j - 1], t->col[j]);
+    }
+}
+
+}  // namespace
+
+// Greedy order: the pattern with the fewest matches first, then repeatedly the
+// one with the fewest matches among those sharing a variable with the patterns
+// already taken (any pattern when none does).
+std::vector<uint32_t> plan_order(const mapsq_pattern* bgp, uint32_t n, const PatternRange* ranges) {
+  std::vector<uint32_t> rest(n), order;
+  for (uint32_t i = 0; i < n; ++i) rest[i] = i;
+  auto size_of = [&](uint32_t i) { return ranges[i].hi - ranges[i].lo; };
+  std::stable_sort(rest.begin(), rest.end(), [&](uint32_t a, uint32_t b) { return size_of(a) < size_of(b); });
+  order.push_back(rest.front());
+  rest.erase(rest.begin());
+  uint32_t seen = pattern_var_set(bgp[order[0]]);
+  while (!rest.empty()) {
+    auto it = std::find_if(rest.begin(), rest.end(), [&](uint32_t i) { return (pattern_var_set(bgp[i]) & seen) != 0; });
+    if (it == rest.end()) it = rest.begin();
+    order.push_back(*it);
+    seen |= pattern_var_set(bgp[*it]);
+    rest.erase(it);
+  }
+  return order;
+}
+
+int query_batch(Ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const uint32_t* ns, TableImpl** out) {
+  // one range search for every pattern of every query
+  std::vector<mapsq_pattern> all;
+  std::vector<size_t> off(nq + 1, 0);
+  for (uint32_t q = 0; q < nq; ++q) {
+    if (!bgps[q] || ns[q] == 0) return set_error(ctx, MAPSQ_ERR_INVALID, "NULL or empty BGP %u", q);
+    for (uint32_t i = 0; i < ns[q]; ++i) MQ_TRY(validate_pattern(ctx, bgps[q][i]));
+    all.insert(all.end(), bgps[q], bgps[q] + ns[q]);
+    off[q + 1] = all.size();
+  }
+  if (!ctx->store.loaded) return set_error(ctx, MAPSQ_ERR_INVALID, "no triple store loaded");
+  std::vector<PatternRange> ranges(all.size());
+  MQ_TRY(scan_ranges(ctx, all.data(), uint32_t(all.size()), ranges.data()));
+
+  std::vector<std::vector<uint32_t>> order(nq);
+  std::vector<TableImpl*> acc(nq, nullptr);
+  auto release_all = [&]() {
+    for (auto*& a : acc) {
+      table_release(ctx, a);
+      a = nullptr;
+    }
+  };
+  uint32_t levels = 0;
+  for (uint32_t q = 0; q < nq; ++q) {
+    order[q] = plan_order(bgps[q], ns[q], ranges.data() + off[q]);
+    const uint32_t first = order[q][0];
+    const int rc = scan_emit(ctx, bgps[q][first], ranges[off[q] + first], &acc[q]);
+    if (rc != MAPSQ_OK) {
+      release_all();
+      return rc;
+    }
+    levels = std::max(levels, ns[q] - 1);
+  }
+  // level l: the (l+1)-th pattern of every query that has one, joined in one batch
+  for (uint32_t l = 1; l <= levels; ++l) {
+    std::vector<uint32_t> who;
+    std::vector<TableImpl*> parts;
+    std::vector<const mapsq_table*> L, R;
+    int rc = MAPSQ_OK;
+    for (uint32_t q = 0; q < nq && rc == MAPSQ_OK; ++q) {
+      if (l >= ns[q]) continue;
+      const uint32_t pi = order[q][l];
+      TableImpl* part = nullptr;
+      rc = scan_emit(ctx, bgps[q][pi], ranges[off[q] + pi], &part);
+      if (rc != MAPSQ_OK) break;
+      who.push_back(q);
+      parts.push_back(part);
+      L.push_back(&acc[q]->pub);
+      R.push_back(&part->pub);
+    }
+    std::vector<TableImpl*> joined(who.size(), nullptr);
+    if (rc == MAPSQ_OK) rc = join_batch(ctx, uint32_t(who.size()), L.data(), R.data(), nullptr, joined.data());
+    for (auto* p : parts) table_release(ctx, p);
+    if (rc != MAPSQ_OK) {
+      release_all();
+      return rc;
+    }
+    for (size_t i = 0; i < who.size(); ++i) {
+      table_release(ctx, acc[who[i]]);
+      acc[who[i]] = joined[i];
+    }
+  }
+  for (uint32_t q = 0; q < nq; ++q) {
+    canonical_columns(&acc[q]->pub);
+    out[q] = acc[q];
+  }
+  return MAPSQ_OK;
+}
+
+}  // namespace mapsq
+
+using namespace mapsq;
+
+extern "C" {
+
+int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out) {
+  if (!ctx || !bgp || !out || n == 0)
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument or empty BGP") : MAPSQ_ERR_INVALID;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  TableImpl* t = nullptr;
+  MQ_TRY(query_batch(ctx, 1, &bgp, &n, &t));
+  *out = &t->pub;
+  return MAPSQ_OK;
+}
+
+int mapsq_query_batch(mapsq_ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const uint32_t* n,
+                      mapsq_table** out) {
+  if (!ctx || (nq && (!bgps || !n || !out)))
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (nq == 0) return MAPSQ_OK;
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  std::vector<TableImpl*> t(nq, nullptr);
+  MQ_TRY(query_batch(ctx, nq, bgps, n, t.data()));
+  for (uint32_t q = 0; q < nq; ++q) out[q] = &t[q]->pub;
+  return MAPSQ_OK;
+}
+
+}  // extern "C"

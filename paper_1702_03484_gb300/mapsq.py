@@ -74,6 +74,8 @@ _SIGNATURES = {
     "mapsq_scan_pattern": (C.c_int, [_P, C.POINTER(Pattern), C.POINTER(_TP)]),
     "mapsq_join": (C.c_int, [_P, _TP, _TP, C.POINTER(_TP), C.POINTER(JoinOpts)]),
     "mapsq_query": (C.c_int, [_P, C.POINTER(Pattern), C.c_uint32, C.POINTER(_TP)]),
+    "mapsq_query_batch": (C.c_int, [_P, C.c_uint32, C.POINTER(C.POINTER(Pattern)), C.POINTER(C.c_uint32),
+                                    C.POINTER(_TP)]),
     "mapsq_join_batch": (C.c_int, [_P, C.c_uint32, C.POINTER(_TP), C.POINTER(_TP), C.POINTER(_TP),
                                    C.POINTER(JoinOpts)]),
     "mapsq_table_from_columns": (C.c_int, [_P, C.c_uint64, C.c_uint32, C.POINTER(C.c_int32), C.POINTER(_P), C.c_int,
@@ -190,6 +192,16 @@ def mapsq_join_batch(ctx, lefts, rights, opts=None):
     outs = (_TP * max(k, 1))()
     _check(ctx, lib().mapsq_join_batch(ctx, k, la, ra, outs, C.byref(opts) if opts else None))
     return [outs[j] for j in range(k)]
+
+
+def mapsq_query_batch(ctx, bgps):
+    nq = len(bgps)
+    arrs = [(Pattern * len(b))(*[_pattern(tp) for tp in b]) for b in bgps]
+    ptrs = (C.POINTER(Pattern) * max(nq, 1))(*[C.cast(a, C.POINTER(Pattern)) for a in arrs])
+    ns = (C.c_uint32 * max(nq, 1))(*[len(b) for b in bgps])
+    outs = (_TP * max(nq, 1))()
+    _check(ctx, lib().mapsq_query_batch(ctx, nq, ptrs, ns, outs))
+    return [outs[q] for q in range(nq)]
 
 
 def mapsq_query(ctx, bgp):
@@ -373,6 +385,9 @@ class Context:
     def join_batch(self, lefts, rights, opts=None):
         return [TableRef(self, p) for p in mapsq_join_batch(self.handle, [x.ptr for x in lefts],
                                                              [x.ptr for x in rights], opts)]
+
+    def query_batch(self, bgps):
+        return [TableRef(self, p) for p in mapsq_query_batch(self.handle, bgps)]
 
     def query(self, bgp) -> TableRef:
         return TableRef(self, mapsq_query(self.handle, bgp))

@@ -141,6 +141,22 @@ def test_query_generated_bgps(ctx, small_graph):
         res.free()
 
 
+def test_query_batch_matches_oracle(ctx, small_graph):
+    """Batched BGP evaluation: every query of the batch equals the oracle."""
+    s, p, o = small_graph
+    ctx.load_triples(s, p, o)
+    G = oracle.distinct_triples(s, p, o)
+    bgps = [b["patterns"] for b in generate_bgps(GraphIndex(s, p, o), 24, seed=19)]
+    bgps.append([(0, 6, 0, 5)])                       # one pattern, repeated variable
+    bgps.append([(5, 99, 1, 4), (1, 6, 2, 5)])        # a pattern with no match
+    res = ctx.query_batch(bgps)
+    assert len(res) == len(bgps)
+    for b, r in zip(bgps, res):
+        assert_same_multiset(r, oracle.evaluate_bgp(G, b, is_set=True), str(b))
+        r.free()
+    assert ctx.query_batch([]) == []
+
+
 def test_query_order_invariance(ctx, small_graph):
     s, p, o = small_graph
     ctx.load_triples(s, p, o)
@@ -171,10 +187,13 @@ def test_university_bgps_full_size(ctx):
     G = oracle.distinct_triples(s, p, o)
     bgps = generate_bgps(GraphIndex(s, p, o), 32, seed=2)
     total = 0
-    for b in bgps:
+    batched = ctx.query_batch([b["patterns"] for b in bgps])
+    for b, rb in zip(bgps, batched):
         res = ctx.query(b["patterns"])
         want = oracle.evaluate_bgp(G, b["patterns"], is_set=True)
         assert_same_multiset(res, want, str(b["patterns"]))
+        assert_same_multiset(rb, want, "batched " + str(b["patterns"]))
         total += res.nrows
         res.free()
+        rb.free()
     assert total > 0
