@@ -6,12 +6,18 @@ evaluated once through ``mapsq_query``: pattern scans, joins, result tables).
 Metric: output bindings/s (one binding = one solution row of a BGP).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload university_bgp|skewed_join|pairwise_uniform]
+                  [--workload university_bgp|skewed_join|pairwise_uniform|uneven_batch|serving]
 
 ``--impl reference`` times the CPU oracle on the host cores on a bounded
 sample of the same workload per step (the paper has no code to run).
 Under torchrun (N > 1) every rank evaluates the whole workload on its own GPU
 (independent replicas; weak scaling, no collective on the data path).
+
+Other workloads: ``skewed_join`` (one 2^26 x 2^24 join, Zipf 1.1 on a 64-bit
+key), ``pairwise_uniform`` (16384 x 8192), ``uneven_batch`` (256 joins of
+uneven size in one mapsq_join_batch, against the same joins one by one) and
+``serving`` (a Poisson stream of 2000 queries/s over 1e8 triples through the
+serving loop; p50/p99 latency, against serial mapsq_query).
 """
 from __future__ import annotations
 
@@ -44,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)  # at least 2: the last one is profiled
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="university_bgp",
-                    choices=["university_bgp", "skewed_join", "pairwise_uniform"])
+                    choices=["university_bgp", "skewed_join", "pairwise_uniform", "uneven_batch", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -93,12 +99,14 @@ class UniversityBGP(Workload):
             t.free()
         return rows
 
-    def run_gpu_batched(self, ctx):
+    def run_gpu_alt(self, ctx):
         rows = 0
         for t in ctx.query_batch(self.bgps):
             rows += t.nrows
             t.free()
         return rows
+
+    alt_form = "batched: mapsq_query_batch, all BGPs of the step in one batch, one batched join per level"
 
     def run_e2e(self, ctx):
         rows = h2d = d2h = 0
@@ -199,7 +207,193 @@ class PairwiseUniform(Workload):
         return oracle.join_mapreduce(self.L, self.R)[1].shape[0], 1
 
 
-WORKLOADS = {"university_bgp": UniversityBGP, "skewed_join": SkewedJoin, "pairwise_uniform": PairwiseUniform}
+class UnevenBatch(Workload):
+    """256 independent joins of uneven size (rows log-uniform in [2^8, 2^22] per
+    side, 2-4 columns, left keys uniform or Zipf(0.8 / 1.2)): one step = the
+    whole batch through ``mapsq_join_batch`` (every phase one launch for all
+    joins); the alternative form runs the same joins one ``mapsq_join`` after
+    another."""
+    name = "uneven_batch"
+
+    def __init__(self, seed=4, n_joins=256):
+        self.joins = [(L, R) for L, R, _ in gen.uneven_batch(seed=seed, n_joins=n_joins)]
+        self.config = {"workload": "uneven_batch", "joins": n_joins, "rows_per_side": "2^U[8,22]",
+                       "columns": "2-4", "zipf_s": "0 / 0.8 / 1.2 per join", "seed": seed,
+                       "form": "mapsq_join_batch (all joins in one batch)",
+                       "l2": "inputs larger than L2, flushed between steps"}
+
+    def setup_gpu(self, ctx):
+        import torch
+        self.dev = [(ctx.table(L.vars, [torch.from_numpy(c).cuda() for c in L.cols]),
+                     ctx.table(R.vars, [torch.from_numpy(c).cuda() for c in R.cols])) for L, R in self.joins]
+
+    def run_gpu(self, ctx):
+        rows = 0
+        for t in ctx.join_batch([a for a, _ in self.dev], [b for _, b in self.dev]):
+            rows += t.nrows
+            t.free()
+        return rows
+
+    def run_gpu_alt(self, ctx):
+        rows = 0
+        for a, b in self.dev:
+            t = ctx.join(a, b)
+            rows += t.nrows
+            t.free()
+        return rows
+
+    alt_form = "plain: the same 256 joins one mapsq_join after another"
+
+    def run_e2e(self, ctx):
+        tabs = [(ctx.table(L.vars, L.cols), ctx.table(R.vars, R.cols)) for L, R in self.joins]
+        h2d = sum(c.nbytes for L, R in self.joins for c in L.cols + R.cols)
+        rows = d2h = 0
+        for t in ctx.join_batch([a for a, _ in tabs], [b for _, b in tabs]):
+            vars_, cols = t.to_host()
+            d2h += sum(c.nbytes for c in cols)
+            rows += t.nrows
+            t.free()
+        for a, b in tabs:
+            a.free()
+            b.free()
+        return rows, h2d, d2h
+
+    def run_oracle(self, sample_index, budget_s=2.0):
+        import oracle
+        rows, done, t0 = 0, 0, time.perf_counter()
+        k = sample_index
+        while time.perf_counter() - t0 < budget_s and done < len(self.joins):
+            L, R = self.joins[k % len(self.joins)]
+            rows += oracle.join_mapreduce(L, R)[1].shape[0]
+            k += 1
+            done += 1
+        return rows, done
+
+
+WORKLOADS = {"university_bgp": UniversityBGP, "skewed_join": SkewedJoin, "pairwise_uniform": PairwiseUniform,
+             "uneven_batch": UnevenBatch}
+
+
+class Serving(UniversityBGP):
+    """Served form: a Poisson stream of BGP queries (mean ``rate`` per second,
+    3-8 patterns, star and chain, 1-2 constants, drawn from a pool of witness
+    BGPs) over a device-resident university graph of 1e8 triples, evaluated by
+    the library's serving loop with continuous batching and a 40 GB budget for
+    the tables in flight.  One step = ``step_s`` seconds of arrivals."""
+    name = "serving"
+
+    def __init__(self, n_triples=100_000_000, pool=2048, seed=5, rate=2000.0, step_s=1.5, budget=40 << 30):
+        self.s, self.p, self.o = gen.university_graph(n_triples, seed=2)
+        g = GraphIndex(self.s, self.p, self.o)
+        self.bgps = [b["patterns"] for b in generate_bgps(g, pool, seed=seed, k_range=(3, 8), var_range=None)]
+        del g
+        self.seed, self.rate, self.step_s, self.budget = seed, rate, step_s, budget
+        self.config = {"workload": "serving", "triples": n_triples, "predicates": 18, "arrivals": "Poisson",
+                       "rate_qps": rate, "step_s": step_s, "patterns_per_bgp": "3-8", "bgp_pool": pool,
+                       "bgp_seed": seed, "mem_budget_gb": budget / (1 << 30), "max_active": 256,
+                       "l2": "store (1e8 triples, 1.6 GB) larger than L2"}
+        self._graph_set = None
+
+    def stream(self, n_steps, part):
+        """Arrival offsets (s) and pool indices of ``n_steps`` steps of arrivals."""
+        r = gen.Rng(self.seed, 100 + part)
+        n = int(self.rate * self.step_s * n_steps * 1.3) + 64
+        t = np.cumsum(-np.log1p(-r.unit(n)) / self.rate)
+        t = t[t < n_steps * self.step_s]
+        return t, r.below(t.shape[0], len(self.bgps))
+
+    def serve(self, ctx, n_steps, part, to_host=False):
+        """Serve one stream; returns (rows, seconds, device ms, h2d, d2h, counters)."""
+        import torch
+        arrivals, idx = self.stream(n_steps, part)
+        ctx.serve_start(max_active=256, mem_budget_bytes=self.budget)
+        tickets = []
+        h2d = [0]
+
+        def producer():
+            t0 = time.perf_counter()
+            for a, i in zip(arrivals.tolist(), idx.tolist()):
+                wait = t0 + a - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                b = self.bgps[i]
+                tickets.append(ctx.submit(b))
+                h2d[0] += 16 * len(b)
+
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        th = threading.Thread(target=producer)
+        ev0.record(stream)
+        w0 = time.perf_counter()
+        th.start()
+        rows = d2h = seen = failed = 0
+        pending = []
+        while th.is_alive() or seen < len(tickets) or pending:
+            while seen < len(tickets):
+                pending.append(tickets[seen])
+                seen += 1
+            still = []
+            for tk in pending:
+                try:
+                    res = ctx.poll(tk)
+                except Exception:
+                    failed += 1
+                    continue
+                if res is None:
+                    still.append(tk)
+                    continue
+                rows += res.nrows
+                if to_host:
+                    _, cols = res.to_host()
+                    d2h += sum(c.nbytes for c in cols)
+                res.free()
+            pending = still
+            time.sleep(0.0005)
+        th.join()
+        ev1.record(stream)
+        ev1.synchronize()
+        wall = time.perf_counter() - w0
+        counters = ctx.serve_stats()
+        ctx.serve_stop()
+        counters["poll_failed"] = failed
+        return rows, wall, ev0.elapsed_time(ev1), h2d[0], d2h, counters, idx
+
+    def run_serial(self, ctx, idx, budget_s=8.0):
+        """The same queries one mapsq_query after another (bounded sample)."""
+        import torch
+        stream = torch.cuda.current_stream()
+        rows, n, ms = 0, 0, 0.0
+        t0 = time.perf_counter()
+        for i in idx.tolist():
+            if time.perf_counter() - t0 > budget_s:
+                break
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t = ctx.query(self.bgps[i])
+            rows += t.nrows
+            t.free()
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+            n += 1
+        return rows, n, ms
+
+    def run_oracle(self, sample_index, budget_s=2.0):
+        import oracle
+        if self._graph_set is None:
+            self._graph_set = oracle.distinct_triples(self.s, self.p, self.o)
+        _, idx = self.stream(1, 0)
+        rows, done, t0 = 0, 0, time.perf_counter()
+        k = sample_index
+        while time.perf_counter() - t0 < budget_s and done < idx.shape[0]:
+            b = self.bgps[int(idx[k % idx.shape[0]])]
+            rows += oracle.evaluate_bgp(self._graph_set, b, is_set=True)[1].shape[0]
+            k += 1
+            done += 1
+        return rows, done
+
+
+WORKLOADS["serving"] = Serving
 
 
 # ---------------------------------------------------------------- helpers
@@ -382,23 +576,23 @@ def run_ours(args):
         ctx.set_profiling(False)
         ctx.profile_only(None)
 
-        # the batched form of the same step, when the workload has one
+        # the other form of the same step (batched or plain), when the workload has one
         batched = None
-        if hasattr(w, "run_gpu_batched"):
+        if hasattr(w, "run_gpu_alt"):
             for _ in range(2):
-                w.run_gpu_batched(ctx)
+                w.run_gpu_alt(ctx)
             bms, brows = 0.0, 0
             for _ in range(args.steps):
                 flush.fill_(1)
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                brows += w.run_gpu_batched(ctx)
+                brows += w.run_gpu_alt(ctx)
                 b.record(stream)
                 b.synchronize()
                 bms += a.elapsed_time(b)
             batched = {"value": brows / (bms / 1000.0), "unit": UNIT, "ms_per_step": bms / args.steps,
-                       "form": "mapsq_query_batch: all BGPs of the step in one batch, one batched join per level"}
+                       "form": w.alt_form}
 
         # end to end through the C ABI with host buffers
         for _ in range(2):
@@ -447,7 +641,7 @@ def run_ours(args):
             "rows_per_step": rows / args.steps,
             "e2e": {"value": e_rows / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d // e_steps,
                     "d2h_bytes_per_step": d2h // e_steps},
-            "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(), "batched": batched,
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(), "other_form": batched,
             "kernels_last_warmup_step": {k: {"launches": v["launches"], "ms": round(v["device_ms"], 4)}
                                          for k, v in warm_stats.items()}}
     if not args.no_cpu_baseline and world == 1:
@@ -466,10 +660,108 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """The served form: Poisson arrivals through mapsq_submit / mapsq_poll."""
+    import torch
+    from paper_1702_03484_gb300 import Context
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = Serving()
+    with Context(device=local) as ctx:
+        w.setup_gpu(ctx)
+        # warm-up stream, profiled in full: it names the kernel with the most device time
+        ctx.reset_stats()
+        ctx.set_profiling(True)
+        w.serve(ctx, max(1, args.warmup // 2), part=1)
+        warm_stats = ctx.kernel_stats()
+        ctx.set_profiling(False)
+        dominant = max(warm_stats.items(), key=lambda kv: kv[1]["device_ms"])[0] if warm_stats else None
+        ctx.reset_stats()
+        ctx.profile_only(dominant)
+        ctx.set_profiling(True)
+        launches0 = ctx.launch_count()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clocks:
+            rows, wall, dev_ms, _, _, counters, idx = w.serve(ctx, args.steps, part=2)
+        torch.cuda.synchronize()
+        launches = ctx.launch_count() - launches0
+        stats = ctx.kernel_stats()
+        ctx.set_profiling(False)
+        ctx.profile_only(None)
+        # the same stream's queries one after another (bounded sample)
+        s_rows, s_n, s_ms = w.run_serial(ctx, idx)
+        # end to end: a shorter stream whose every result is copied to the host
+        e_steps = max(1, min(args.steps, 4))
+        e_rows, e_wall, _, h2d, d2h, e_counters, _ = w.serve(ctx, e_steps, part=3, to_host=True)
+
+    t_max, rows_all = dev_ms, rows
+    if world > 1:
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        r = torch.tensor([rows], device="cuda", dtype=torch.float64)
+        dist.all_reduce(r)
+        t_max, rows_all = float(t.item()), float(r.item())
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    roofline = None
+    if stats:
+        name, st = max(stats.items(), key=lambda kv: kv[1]["device_ms"])
+        per_launch_s = st["device_ms"] / 1000.0 / st["launches"]
+        achieved = st["alg_bytes"] / st["launches"] / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": ncu_traffic(name, w.name), "launches": st["launches"],
+                    "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
+                    "share_of_device_time": warm_stats[name]["device_ms"] / sum(v["device_ms"]
+                                                                                for v in warm_stats.values())}
+    line = {"metric": METRIC, "value": rows_all / (t_max / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": w.config,
+            "serving": {"queries": counters["submitted"], "completed": counters["completed"],
+                        "failed": counters["failed"], "p50_ms": counters["p50_ms"], "p99_ms": counters["p99_ms"],
+                        "mean_ms": counters["mean_ms"], "rounds": counters["rounds"],
+                        "batched_joins": counters["batched_joins"], "preempted": counters["preempted"],
+                        "achieved_qps": counters["submitted"] / wall, "wall_s": wall},
+            "serial_plain": {"value": s_rows / (s_ms / 1000.0) if s_ms else None, "unit": UNIT, "queries": s_n,
+                             "ms_per_query": s_ms / max(s_n, 1),
+                             "form": "the same stream's queries one mapsq_query after another"},
+            "e2e": {"value": e_rows / e_wall, "unit": UNIT, "h2d_bytes_per_step": h2d // e_steps,
+                    "d2h_bytes_per_step": d2h // e_steps, "p50_ms": e_counters["p50_ms"],
+                    "p99_ms": e_counters["p99_ms"]},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(),
+            "kernels_warmup_stream": {k: {"launches": v["launches"], "ms": round(v["device_ms"], 4)}
+                                      for k, v in warm_stats.items()}}
+    if not args.no_cpu_baseline and world == 1:
+        w.run_oracle(0, budget_s=0.0)  # builds the oracle's triple set, not timed
+        t0 = time.perf_counter()
+        crow, cunits, k = 0, 0, 0
+        while time.perf_counter() - t0 < 15.0:
+            r, u = w.run_oracle(k, budget_s=15.0 - (time.perf_counter() - t0))
+            crow += r
+            cunits += u
+            k += u
+        cdt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": crow / cdt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{cunits} queries of the serving stream in {cdt:.1f} s, evaluated "
+                                          f"one after another by the numpy oracle, single thread"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

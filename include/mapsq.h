@@ -108,6 +108,25 @@ typedef struct {
   int32_t reserved;
 } mapsq_join_opts;
 
+/* Serving loop options (mapsq_serve_start); zero fields choose defaults. */
+typedef struct {
+  uint32_t max_active;        /* queries in flight at once (default 256) */
+  uint32_t reserved0;
+  uint64_t mem_budget_bytes;  /* bytes of intermediate and result tables in flight (0 = unbounded) */
+  uint64_t reserved[4];
+} mapsq_serve_opts;
+
+/* Serving loop counters (mapsq_serve_stats).  Latency is measured from
+ * mapsq_submit to the query's completion, over completed and failed queries. */
+typedef struct {
+  uint64_t submitted, completed, failed, in_flight;
+  uint64_t rounds;         /* worker rounds (each at most one batched join) */
+  uint64_t batched_joins;  /* joins run inside those batches */
+  uint64_t result_rows;    /* rows of the completed results */
+  uint64_t preempted;      /* queries put back in the queue for memory */
+  double p50_ms, p99_ms, mean_ms;
+} mapsq_serve_counters;
+
 /* Per-kernel device time, collected while profiling is on (mapsq_set_profiling).
  * ``alg_bytes`` sums each launch's algorithmic bytes: the bytes the step must
  * read and write at minimum (inputs once, outputs once). */
@@ -199,6 +218,47 @@ MAPSQ_API int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, 
  * All or nothing: on error no table is returned.  Errors: as mapsq_query. */
 MAPSQ_API int mapsq_query_batch(mapsq_ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const uint32_t* n,
                                 mapsq_table** out);
+
+/* Start the serving loop: a worker thread that evaluates submitted BGP queries
+ * with continuous batching over the loaded store.  Each query is evaluated as
+ * in mapsq_query (Section 2: the host hands the partial-match tables of one
+ * query, pattern after pattern, to the device join); running many queries at
+ * once, in shared launches under a memory budget, has no counterpart in the
+ * paper.  In every round it admits
+ * waiting queries (while fewer than max_active are in flight and the tables
+ * in flight stay under mem_budget_bytes), gives the new ones their range
+ * searches in one launch, and puts the next join of every query in flight into
+ * one batched join; after that batch's count pass, results are written in
+ * arrival order while they fit in the budget, the others wait for a later
+ * round.  When no join fits, the youngest query in flight is put back in the
+ * queue (its tables freed) and admissions pause until a join is written; a
+ * query whose next result cannot fit beside its own tables even alone fails
+ * with MAPSQ_ERR_BUDGET.  While serving, only the serve calls, mapsq_table_to_host,
+ * mapsq_table_free, mapsq_memory_in_use and the statistics calls may be made
+ * on the context; the others return MAPSQ_ERR_BUSY.  Errors: BUSY (already
+ * serving), INVALID (no store), OOM. */
+MAPSQ_API int mapsq_serve_start(mapsq_ctx* ctx, const mapsq_serve_opts* opts);
+
+/* Queue a BGP of ``n`` patterns (copied); *ticket identifies it.  Thread-safe.
+ * Errors: BUSY (not serving or stopping), INVALID, UNSUPPORTED. */
+MAPSQ_API int mapsq_submit(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, uint64_t* ticket);
+
+/* Collect a query: MAPSQ_OK with *out = its result (written on the device;
+ * columns in ascending variable id; owned by the caller until
+ * mapsq_table_free) once done, MAPSQ_OK
+ * with *out = NULL while it runs, the query's error code if it failed,
+ * NOT_FOUND for a ticket never issued.  A result is returned once.
+ * Thread-safe. */
+MAPSQ_API int mapsq_poll(mapsq_ctx* ctx, uint64_t ticket, mapsq_table** out);
+
+/* Counters and latency percentiles of the serving loop.  Thread-safe. */
+MAPSQ_API int mapsq_serve_stats(mapsq_ctx* ctx, mapsq_serve_counters* out);
+
+/* Finish every submitted query, then stop the worker.  Results not yet
+ * collected stay owned by the context.  Not to be called while another thread
+ * is inside mapsq_submit, mapsq_poll or mapsq_serve_stats on this context.
+ * Errors: BUSY (not serving). */
+MAPSQ_API int mapsq_serve_stop(mapsq_ctx* ctx);
 
 /* Copy ``ncols`` columns of ``nrows`` rows (host pointers, or device pointers if
  * ``on_device``) into a new library-owned device table with variables ``var``.

@@ -284,6 +284,7 @@ int mapsq_create(mapsq_ctx** out, int device, const mapsq_allocator* allocator, 
 
 int mapsq_destroy(mapsq_ctx* ctx) {
   if (!ctx) return MAPSQ_OK;
+  server_shutdown(ctx);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (auto& r : ctx->pending) {
@@ -308,6 +309,7 @@ int mapsq_destroy(mapsq_ctx* ctx) {
 
 int mapsq_set_stream(mapsq_ctx* ctx, void* cuda_stream) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   ctx->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->own_stream;
   return MAPSQ_OK;
 }
@@ -315,6 +317,7 @@ int mapsq_set_stream(mapsq_ctx* ctx, void* cuda_stream) {
 int mapsq_load_triples(mapsq_ctx* ctx, const uint32_t* s, const uint32_t* p, const uint32_t* o, uint64_t n,
                        int ptrs_on_device) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   if (n && (!s || !p || !o)) return set_error(ctx, MAPSQ_ERR_INVALID, "NULL triple column");
   if (n >= (uint64_t(1) << 32)) return set_error(ctx, MAPSQ_ERR_INVALID, "at most 2^32-1 triples");
   MQ_CUDA(cudaSetDevice(ctx->device));
@@ -323,6 +326,7 @@ int mapsq_load_triples(mapsq_ctx* ctx, const uint32_t* s, const uint32_t* p, con
 
 int mapsq_store_info(mapsq_ctx* ctx, uint64_t* n_triples, uint32_t* n_predicates) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   if (n_triples) *n_triples = ctx->store.n;
   if (n_predicates) *n_predicates = uint32_t(ctx->store.pred_id.size());
   return MAPSQ_OK;
@@ -330,6 +334,7 @@ int mapsq_store_info(mapsq_ctx* ctx, uint64_t* n_triples, uint32_t* n_predicates
 
 int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_table** out) {
   if (!ctx || !tp || !out) return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   MQ_CUDA(cudaSetDevice(ctx->device));
   MQ_TRY(validate_pattern(ctx, *tp));
   if (!ctx->store.loaded) return set_error(ctx, MAPSQ_ERR_INVALID, "no triple store loaded");
@@ -345,6 +350,7 @@ int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right
                const mapsq_join_opts* opts) {
   if (!ctx || !left || !right || !out)
     return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   MQ_CUDA(cudaSetDevice(ctx->device));
   TableImpl* t = nullptr;
   MQ_TRY(join_tables(ctx, left, right, opts, &t));
@@ -356,6 +362,7 @@ int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* left,
                      mapsq_table** out, const mapsq_join_opts* opts) {
   if (!ctx || (k && (!left || !right || !out)))
     return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   MQ_CUDA(cudaSetDevice(ctx->device));
   std::vector<TableImpl*> t(k, nullptr);
   MQ_TRY(join_batch(ctx, k, left, right, opts, t.data()));
@@ -367,6 +374,7 @@ int mapsq_table_from_columns(mapsq_ctx* ctx, uint64_t nrows, uint32_t ncols, con
                              const uint32_t* const* cols, int on_device, mapsq_table** out) {
   if (!ctx || !out || (ncols && (!var || !cols)))
     return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   if (ncols > MAPSQ_MAX_VARS) return set_error(ctx, MAPSQ_ERR_INVALID, "more than 16 columns");
   if (ncols == 0 && nrows > 1) return set_error(ctx, MAPSQ_ERR_INVALID, "a 0-column table has 0 or 1 rows");
   uint32_t seen = 0;
@@ -410,6 +418,7 @@ int mapsq_table_from_columns(mapsq_ctx* ctx, uint64_t nrows, uint32_t ncols, con
 int mapsq_table_to_host(mapsq_ctx* ctx, const mapsq_table* t, uint32_t* const* host_cols) {
   if (!ctx || !t || (t->ncols && !host_cols))
     return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   MQ_CUDA(cudaSetDevice(ctx->device));
   for (uint32_t c = 0; c < t->ncols && t->nrows; ++c) {
     if (!host_cols[c]) return set_error(ctx, MAPSQ_ERR_INVALID, "NULL host column %u", c);
@@ -422,12 +431,14 @@ int mapsq_table_to_host(mapsq_ctx* ctx, const mapsq_table* t, uint32_t* const* h
 
 void mapsq_table_free(mapsq_ctx* ctx, mapsq_table* t) {
   if (!ctx || !t) return;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   TableImpl* impl = reinterpret_cast<TableImpl*>(t);
   table_release(ctx, impl);
 }
 
 int mapsq_sync(mapsq_ctx* ctx) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   MQ_CUDA(cudaSetDevice(ctx->device));
   MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
   MQ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -436,6 +447,7 @@ int mapsq_sync(mapsq_ctx* ctx) {
 
 int mapsq_memory_in_use(mapsq_ctx* ctx, uint64_t* bytes, uint64_t* peak_bytes) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   if (bytes) *bytes = ctx->in_use;
   if (peak_bytes) *peak_bytes = ctx->peak;
   return MAPSQ_OK;
@@ -443,6 +455,7 @@ int mapsq_memory_in_use(mapsq_ctx* ctx, uint64_t* bytes, uint64_t* peak_bytes) {
 
 int mapsq_set_profiling(mapsq_ctx* ctx, int enable) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   if (!enable) MQ_TRY(drain_profile(ctx));
   ctx->profiling = enable != 0;
   return MAPSQ_OK;
@@ -450,6 +463,7 @@ int mapsq_set_profiling(mapsq_ctx* ctx, int enable) {
 
 int mapsq_kernel_stats(mapsq_ctx* ctx, mapsq_kernel_stat* out, uint32_t cap, uint32_t* n) {
   if (!ctx || !n || (cap && !out)) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   MQ_TRY(drain_profile(ctx));
   uint32_t k = 0;
   for (int i = 0; i < K_COUNT_KERNELS; ++i) {
@@ -469,12 +483,14 @@ int mapsq_kernel_stats(mapsq_ctx* ctx, mapsq_kernel_stat* out, uint32_t cap, uin
 
 int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches) {
   if (!ctx || !launches) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   *launches = ctx->launches;
   return MAPSQ_OK;
 }
 
 int mapsq_profile_only(mapsq_ctx* ctx, const char* name) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   if (!name) {
     ctx->profile_only = -1;
     return MAPSQ_OK;
@@ -489,6 +505,7 @@ int mapsq_profile_only(mapsq_ctx* ctx, const char* name) {
 
 int mapsq_reset_stats(mapsq_ctx* ctx) {
   if (!ctx) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   MQ_TRY(drain_profile(ctx));
   for (auto& t : ctx->totals) t = KernelTotals{};
   return MAPSQ_OK;

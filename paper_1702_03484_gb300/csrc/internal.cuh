@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -85,8 +86,14 @@ struct KernelTotals {
 
 }  // namespace mapsq
 
+namespace mapsq {
+struct Server;
+}
+
 struct mapsq_ctx {
   int device = 0;
+  std::recursive_mutex mu;           // held by the serving loop for a round, and by calls that may run meanwhile
+  mapsq::Server* server = nullptr;   // serving loop, while started
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;
   bool has_allocator = false;
@@ -178,6 +185,9 @@ int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes);
 // Read a few 64-bit words back from the device (synchronises the stream).
 int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count);
 
+// Serving loop (serve.cu): stops and frees it (mapsq_destroy).
+void server_shutdown(Ctx* ctx);
+
 // Device status word check after a synchronisation.
 int check_status(Ctx* ctx);
 
@@ -206,6 +216,12 @@ int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const maps
                 TableImpl** out);
 int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
                const mapsq_join_opts* opts, TableImpl** out);
+
+// Counts k joins, then writes, in order, those whose results fit together in
+// ``budget_bytes`` (0 = all): status[j] = 0 written (out[j] set), 1 deferred;
+// need[j] = bytes of join j's result table.
+int join_batch_admit(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
+                     uint64_t budget_bytes, TableImpl** out, int* status, uint64_t* need);
 
 // BGP evaluation (query.cu): pattern order, and many BGPs level by level.
 std::vector<uint32_t> plan_order(const mapsq_pattern* bgp, uint32_t n, const PatternRange* ranges);

@@ -727,6 +727,7 @@ struct BatchJoin {
   uint64_t* d_first = nullptr;             // kPhases x (k + 1) item offsets
   std::vector<uint64_t> first;             // host copy
   std::vector<uint64_t> host;              // read-back buffer
+  std::vector<uint8_t> take;               // joins that write() produces (all by default)
   uint32_t k = 0;
 
   int fail(int code, const char* what) { return ctx ? set_error(ctx, code, "%s", what) : code; }
@@ -763,6 +764,7 @@ struct BatchJoin {
 
   int prepare(uint32_t nj, const mapsq_table* const* L, const mapsq_table* const* R) {
     k = nj;
+    take.assign(k, 1);
     plans.assign(k, JoinPlan{});
     descs.assign(k, JoinDesc{});
     first.assign(size_t(kPhases) * (k + 1), 0);
@@ -990,7 +992,7 @@ struct BatchJoin {
       double in = 0;
       for (int c = 0; c < pl.lay.ncols; ++c) {
         const bool fb = pl.lay.side[c] == pl.bside && c >= pl.lay.nkey;
-        d.out[c] = out[j][c];
+        d.out[c] = out[j] ? out[j][c] : nullptr;  // joins not taken have no output table
         if (fb) {
           d.src[c] = pl.cross ? pl.B->col[pl.lay.col[c]] : d.grouped + b++;
           d.from_build |= 1u << c;
@@ -1001,7 +1003,7 @@ struct BatchJoin {
           if (c >= pl.lay.nkey) in += 4.0 * pl.np;
         }
       }
-      if (!pl.T || !pl.lay.ncols) continue;
+      if (!pl.T || !pl.lay.ncols || !take[j]) continue;
       const uint64_t ntiles = ceil_div(pl.T, kWriteTile);
       if (pl.cross) {
         cr[j] = ntiles;
@@ -1065,6 +1067,49 @@ int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_ta
     return rc;
   }
   for (uint32_t j = 0; j < k; ++j) out[j] = tabs[j];
+  return MAPSQ_OK;
+}
+
+int join_batch_admit(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
+                     uint64_t budget_bytes, TableImpl** out, int* status, uint64_t* need) {
+  for (uint32_t j = 0; j < k; ++j) {
+    out[j] = nullptr;
+    status[j] = 1;
+    need[j] = 0;
+  }
+  if (k == 0) return MAPSQ_OK;
+  Scratch scratch(ctx);
+  BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
+  MQ_TRY(bj.prepare(k, L, R));
+  MQ_TRY(bj.count());
+  // admission in order: result tables are written while they fit in the budget
+  uint64_t used = 0;
+  for (uint32_t j = 0; j < k; ++j) {
+    const uint64_t bytes = 4 * ((bj.plans[j].T + 63) & ~uint64_t(63)) * uint64_t(bj.plans[j].lay.ncols);
+    need[j] = bytes;
+    bj.take[j] = 0;
+    if (budget_bytes && used + bytes > budget_bytes) continue;
+    bj.take[j] = 1;
+    used += bytes;
+  }
+  std::vector<TableImpl*> tabs(k, nullptr);
+  std::vector<uint32_t* const*> cols(k, nullptr);
+  int rc = MAPSQ_OK;
+  for (uint32_t j = 0; j < k && rc == MAPSQ_OK; ++j) {
+    if (!bj.take[j]) continue;
+    rc = table_alloc(ctx, bj.plans[j].T, uint32_t(bj.plans[j].lay.ncols), bj.plans[j].lay.var, &tabs[j]);
+    if (rc == MAPSQ_OK) cols[j] = tabs[j]->pub.col;
+  }
+  if (rc == MAPSQ_OK) rc = bj.write(cols.data());
+  if (rc != MAPSQ_OK) {
+    for (auto* t : tabs) table_release(ctx, t);
+    return rc;
+  }
+  for (uint32_t j = 0; j < k; ++j)
+    if (bj.take[j]) {
+      out[j] = tabs[j];
+      status[j] = 0;
+    }
   return MAPSQ_OK;
 }
 

@@ -132,6 +132,7 @@ extern "C" {
 int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out) {
   if (!ctx || !bgp || !out || n == 0)
     return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument or empty BGP") : MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   MQ_CUDA(cudaSetDevice(ctx->device));
   TableImpl* t = nullptr;
   MQ_TRY(query_batch(ctx, 1, &bgp, &n, &t));
@@ -143,6 +144,7 @@ int mapsq_query_batch(mapsq_ctx* ctx, uint32_t nq, const mapsq_pattern* const* b
                       mapsq_table** out) {
   if (!ctx || (nq && (!bgps || !n || !out)))
     return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
   if (nq == 0) return MAPSQ_OK;
   MQ_CUDA(cudaSetDevice(ctx->device));
   std::vector<TableImpl*> t(nq, nullptr);

@@ -61,6 +61,18 @@ class KernelStat(C.Structure):
                 ("alg_bytes", C.c_double)]
 
 
+class ServeOpts(C.Structure):
+    _fields_ = [("max_active", C.c_uint32), ("reserved0", C.c_uint32), ("mem_budget_bytes", C.c_uint64),
+                ("reserved", C.c_uint64 * 4)]
+
+
+class ServeCounters(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("in_flight", C.c_uint64), ("rounds", C.c_uint64), ("batched_joins", C.c_uint64),
+                ("result_rows", C.c_uint64), ("preempted", C.c_uint64), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("mean_ms", C.c_double)]
+
+
 _P = C.c_void_p
 _TP = C.POINTER(Table)
 _SIGNATURES = {
@@ -90,6 +102,11 @@ _SIGNATURES = {
     "mapsq_profile_only": (C.c_int, [_P, C.c_char_p]),
     "mapsq_launch_count": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
     "mapsq_join_noalloc": (C.c_int, [_TP, _TP, C.POINTER(_P), C.c_uint64, _TP, C.POINTER(C.c_uint64), _P]),
+    "mapsq_serve_start": (C.c_int, [_P, C.POINTER(ServeOpts)]),
+    "mapsq_submit": (C.c_int, [_P, C.POINTER(Pattern), C.c_uint32, C.POINTER(C.c_uint64)]),
+    "mapsq_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(_TP)]),
+    "mapsq_serve_stats": (C.c_int, [_P, C.POINTER(ServeCounters)]),
+    "mapsq_serve_stop": (C.c_int, [_P]),
 }
 
 _lib = None
@@ -289,6 +306,39 @@ def mapsq_join_noalloc(left, right, out_cols, capacity, stream=None):
     return rc, out, rows.value
 
 
+def mapsq_serve_start(ctx, max_active=0, mem_budget_bytes=0):
+    opts = ServeOpts(max_active=max_active, mem_budget_bytes=mem_budget_bytes)
+    _check(ctx, lib().mapsq_serve_start(ctx, C.byref(opts)))
+
+
+def mapsq_submit(ctx, bgp):
+    arr = (Pattern * len(bgp))(*[_pattern(tp) for tp in bgp])
+    ticket = C.c_uint64()
+    rc = lib().mapsq_submit(ctx, arr, len(bgp), C.byref(ticket))
+    if rc != 0:
+        raise MapsqError(rc, lib().mapsq_strerror(rc).decode())
+    return ticket.value
+
+
+def mapsq_poll(ctx, ticket):
+    """The query's result table once done (None while it runs); raises its error."""
+    out = _TP()
+    rc = lib().mapsq_poll(ctx, ticket, C.byref(out))
+    if rc != 0:
+        raise MapsqError(rc, lib().mapsq_strerror(rc).decode())
+    return out if out else None
+
+
+def mapsq_serve_stats(ctx):
+    st = ServeCounters()
+    _check(ctx, lib().mapsq_serve_stats(ctx, C.byref(st)))
+    return {name: getattr(st, name) for name, _ in ServeCounters._fields_}
+
+
+def mapsq_serve_stop(ctx):
+    _check(ctx, lib().mapsq_serve_stop(ctx))
+
+
 def table_view(vars_, cols, nrows=None):
     """A ``Table`` struct describing caller-owned device columns (no copy)."""
     t = Table()
@@ -415,6 +465,22 @@ class Context:
 
     def launch_count(self):
         return mapsq_launch_count(self.handle)
+
+    def serve_start(self, max_active=0, mem_budget_bytes=0):
+        mapsq_serve_start(self.handle, max_active, mem_budget_bytes)
+
+    def submit(self, bgp) -> int:
+        return mapsq_submit(self.handle, bgp)
+
+    def poll(self, ticket):
+        p = mapsq_poll(self.handle, ticket)
+        return TableRef(self, p) if p is not None else None
+
+    def serve_stats(self):
+        return mapsq_serve_stats(self.handle)
+
+    def serve_stop(self):
+        mapsq_serve_stop(self.handle)
 
 
 def torch_allocator():
