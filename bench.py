@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--workload", default="university_bgp",
                     choices=["university_bgp", "skewed_join", "pairwise_uniform", "uneven_batch", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default="full", choices=["full", "small"],
+                    help="small: a reduced case of the workload for profiler captures (skewed_join: "
+                         "2^24 x 2^22 rows over 2^20 key ids)")
     return ap.parse_args()
 
 
@@ -396,6 +399,14 @@ class Serving(UniversityBGP):
 WORKLOADS["serving"] = Serving
 
 
+def make_workload(args):
+    if args.size == "small":
+        if args.workload != "skewed_join":
+            raise SystemExit("--size small exists for skewed_join only")
+        return SkewedJoin(log_a=24, log_b=22, log_keys=20)
+    return WORKLOADS[args.workload]()
+
+
 # ---------------------------------------------------------------- helpers
 
 def dist_env():
@@ -500,7 +511,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = WORKLOADS[args.workload]()
+    w = make_workload(args)
     for i in range(args.warmup):
         w.run_oracle(i, budget_s=0.5)
     rows, units, t0 = 0, 0, time.perf_counter()
@@ -531,7 +542,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = WORKLOADS[args.workload]()
+    w = make_workload(args)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
     def barrier():

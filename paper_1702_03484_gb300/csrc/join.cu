@@ -46,7 +46,8 @@ constexpr int kRowTile = 2048;                         // rows per work item (bu
 constexpr int kRowItems = kRowTile / kThreads;         // rows per thread
 constexpr int kWriteRows = 16;                         // output rows per thread per write tile
 constexpr int kWriteTile = kThreads * kWriteRows;      // output rows per write tile
-constexpr int kStageRows = 1800;                       // probe rows staged per write tile (48 KB of shared memory in all)
+constexpr int kStageRows = 1800;                       // probe rows per stage chunk (48 KB of shared memory in all)
+constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
 constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
 constexpr int kHllBits = 12;
 constexpr int kHllRegs = 1 << kHllBits;
@@ -134,10 +135,17 @@ __device__ __forceinline__ uint32_t home_bucket(uint64_t key, uint32_t M) {
   return uint32_t((uint64_t(h * 0x85ebca6bu) * uint64_t(M / kBucket)) >> 32);
 }
 
+__device__ __forceinline__ uint64_t* bucket_keys(const HashTable& t, uint32_t b) {
+  return t.keys + uint64_t(b) * kBucket;
+}
+
+// Group entry {count, begin within the slot tile} of slot s.
+__device__ __forceinline__ uint2* group_of(const HashTable& t, uint32_t s) { return t.group + s; }
+
 __device__ __forceinline__ void load_bucket(const HashTable& t, uint64_t key, uint32_t* b, ulonglong2* k01,
                                             ulonglong2* k23) {
   *b = home_bucket(key, t.M);
-  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.keys + uint64_t(*b) * kBucket);
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(bucket_keys(t, *b));
   *k01 = __ldg(p);
   *k23 = __ldg(p + 1);
 }
@@ -159,7 +167,7 @@ __device__ __forceinline__ uint32_t find_slot(const HashTable& t, uint64_t key, 
       return (hit >> j) & 1u ? b * kBucket + j : kNoSlot;
     }
     b = b + 1 == nbk ? 0 : b + 1;
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.keys + uint64_t(b) * kBucket);
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(bucket_keys(t, b));
     k01 = __ldg(p);
     k23 = __ldg(p + 1);
   }
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(kThreads) hash_insert_kernel(const JoinDesc* _
       } else {
         uint32_t b = home_bucket(key, t.M);
         for (uint32_t n = 0; n < nbk && s == kNoSlot; ++n) {
-          uint64_t* bkt = t.keys + uint64_t(b) * kBucket;
+          uint64_t* bkt = bucket_keys(t, b);
           const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt));
           const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt) + 1);
           const uint64_t kk[4] = {k01.x, k01.y, k23.x, k23.y};
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(kThreads) hash_insert_kernel(const JoinDesc* _
     const unsigned peers = __match_any_sync(0xffffffffu, s);
     const int leader = __ffs(peers) - 1;
     uint32_t base_rank = 0;
-    if (lane == unsigned(leader) && valid && s != kNoSlot) base_rank = atomicAdd(&t.group[s].x, __popc(peers));
+    if (lane == unsigned(leader) && valid && s != kNoSlot) base_rank = atomicAdd(&group_of(t, s)->x, __popc(peers));
     base_rank = __shfl_sync(0xffffffffu, base_rank, leader);
     if (valid) {
       d.slot_of[i] = s;
@@ -302,7 +310,7 @@ __global__ void __launch_bounds__(kThreads) slot_scan_kernel(const JoinDesc* __r
 #pragma unroll
   for (int it = 0; it < kRowItems; ++it) {
     const uint64_t s = base + uint64_t(threadIdx.x) * kRowItems + it;
-    c[it] = s < n ? d.t.group[s].x : 0u;
+    c[it] = s < n ? group_of(d.t, uint32_t(s))->x : 0u;
     sum += c[it];
   }
   uint64_t total;
@@ -310,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) slot_scan_kernel(const JoinDesc* __r
 #pragma unroll
   for (int it = 0; it < kRowItems; ++it) {
     const uint64_t s = base + uint64_t(threadIdx.x) * kRowItems + it;
-    if (s < n && c[it]) d.t.group[s].y = uint32_t(run);
+    if (s < n && c[it]) group_of(d.t, uint32_t(s))->y = uint32_t(run);
     run += c[it];
   }
   if (threadIdx.x == 0) d.slot_total[blockIdx.x - first[j]] = total;
@@ -380,7 +388,7 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (s[q] != kNoSlot) pos[q] += group_begin(d.t, s[q], d.t.group[s[q]].y);
+      if (s[q] != kNoSlot) pos[q] += group_begin(d.t, s[q], group_of(d.t, s[q])->y);
     for (int c = 0; c < nbv; ++c) {
       uint32_t x[4];
 #pragma unroll
@@ -433,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc
     for (int q = 0; q < 4; ++q) {
       const int loc = (h0 + q) * kThreads + threadIdx.x;
       const uint64_t row = base + loc;
-      const uint2 g = s[q] != kNoSlot ? t.group[s[q]] : make_uint2(0u, 0u);
+      const uint2 g = s[q] != kNoSlot ? *group_of(t, s[q]) : make_uint2(0u, 0u);
       if (row < np) __stcs(d.pbeg + row, g.x ? group_begin(t, s[q], g.y) : 0u);
       s_cnt[pad(loc)] = g.x;
     }
@@ -514,19 +522,75 @@ __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t 
   return lo;
 }
 
-// One output column of a tile: row j * kThreads + tid takes src[idx[j] * stride];
-// the gathers are issued before the coalesced streaming stores.
+// Output rows of a write tile are handled in runs of kVec consecutive rows: run
+// g * kThreads + tid of the tile belongs to thread tid, so a warp's stores of
+// one column cover 512 contiguous bytes (16-byte stores; columns and tiles are
+// 16-byte aligned).  Entry g * kVec + w of a thread's arrays is row
+// (g * kThreads + tid) * kVec + w.
+constexpr int kVec = 4;
+constexpr int kRuns = kWriteRows / kVec;
+
+__device__ __forceinline__ uint32_t run_row(int i) {
+  return (uint32_t(i / kVec) * kThreads + threadIdx.x) * kVec + uint32_t(i % kVec);
+}
+
+template <bool kFull>
+__device__ __forceinline__ void store_runs(uint32_t* __restrict__ dst, const uint32_t (&x)[kWriteRows], uint32_t n) {
+#pragma unroll
+  for (int g = 0; g < kRuns; ++g) {
+    const uint32_t q = (uint32_t(g) * kThreads + threadIdx.x) * kVec;
+    if (kFull || q + kVec <= n) {
+      __stcs(reinterpret_cast<uint4*>(dst + q), make_uint4(x[g * kVec], x[g * kVec + 1], x[g * kVec + 2], x[g * kVec + 3]));
+    } else {
+#pragma unroll
+      for (int w = 0; w < kVec; ++w)
+        if (q + w < n) __stcs(dst + q + w, x[g * kVec + w]);
+    }
+  }
+}
+
+// One output column of a tile: row run_row(i) takes src[idx[i] * stride]; the
+// gathers are issued before the stores.
 template <bool kFull>
 __device__ __forceinline__ void write_column(const uint32_t* __restrict__ src, const uint32_t (&idx)[kWriteRows],
                                              uint32_t stride, uint32_t* __restrict__ dst, uint32_t n) {
   uint32_t x[kWriteRows];
 #pragma unroll
-  for (int j = 0; j < kWriteRows; ++j)
-    x[j] = kFull || uint32_t(j) * kThreads + threadIdx.x < n ? __ldg(src + uint64_t(idx[j]) * stride) : 0u;
-  uint32_t* dd = dst + threadIdx.x;
+  for (int i = 0; i < kWriteRows; ++i)
+    x[i] = kFull || run_row(i) < n ? __ldg(src + uint64_t(idx[i]) * stride) : 0u;
+  store_runs<kFull>(dst, x, n);
+}
+
+// Two build-side columns stored together (row-major pairs): one 8-byte gather
+// per row feeds both; half of the thread's runs at a time.
+template <bool kFull>
+__device__ __forceinline__ void write_pair(const uint32_t* __restrict__ grouped, const uint32_t (&idx)[kWriteRows],
+                                           uint32_t* __restrict__ dst0, uint32_t* __restrict__ dst1, uint32_t n) {
+  constexpr int kHalf = kWriteRows / 2;
 #pragma unroll
-  for (int j = 0; j < kWriteRows; ++j)
-    if (kFull || uint32_t(j) * kThreads + threadIdx.x < n) __stcs(dd + j * kThreads, x[j]);
+  for (int h = 0; h < 2; ++h) {
+    uint2 v[kHalf];
+#pragma unroll
+    for (int i = 0; i < kHalf; ++i)
+      v[i] = kFull || run_row(h * kHalf + i) < n ? __ldg(reinterpret_cast<const uint2*>(grouped) + idx[h * kHalf + i])
+                                                 : make_uint2(0u, 0u);
+#pragma unroll
+    for (int g = 0; g < kRuns / 2; ++g) {
+      const uint32_t q = (uint32_t(h * kRuns / 2 + g) * kThreads + threadIdx.x) * kVec;
+      const uint2* r = v + g * kVec;
+      if (kFull || q + kVec <= n) {
+        __stcs(reinterpret_cast<uint4*>(dst0 + q), make_uint4(r[0].x, r[1].x, r[2].x, r[3].x));
+        __stcs(reinterpret_cast<uint4*>(dst1 + q), make_uint4(r[0].y, r[1].y, r[2].y, r[3].y));
+      } else {
+#pragma unroll
+        for (int w = 0; w < kVec; ++w)
+          if (q + w < n) {
+            __stcs(dst0 + q + w, r[w].x);
+            __stcs(dst1 + q + w, r[w].y);
+          }
+      }
+    }
+  }
 }
 
 // Write phase, persistent: CTAs take write items (a join and one of its output
@@ -536,7 +600,7 @@ __device__ __forceinline__ void write_column(const uint32_t* __restrict__ src, c
 // thread maps 16 consecutive output rows to (probe row, build row) with one
 // 32-bit search and a short walk, into a padded row map; (3) every thread takes
 // 16 rows striped over the block (a row per lane), reads their map entries once
-// per side, and writes the columns with coalesced streaming stores.
+// per side, and writes the columns with 16-byte streaming stores.
 __global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                                  uint32_t k, unsigned long long* __restrict__ queue) {
   __shared__ uint32_t s_rel[kStageRows + 1];
@@ -560,56 +624,68 @@ __global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc*
     const uint64_t t0 = tile * kWriteTile;
     const uint32_t n = uint32_t(min(uint64_t(kWriteTile), d.T - t0));
     const uint64_t ilo = d.part[tile];
-    const uint64_t nst = d.part[tile + 1] - ilo + 1;  // probe rows ilo .. part[tile + 1] can feed this tile
+    const uint64_t ihi = d.part[tile + 1] + 1;  // probe rows [ilo, ihi) can feed this tile
     const uint32_t q0 = threadIdx.x * kWriteRows;
-    if (nst <= kStageRows) {
-      const uint32_t ns = uint32_t(nst);
-      for (uint32_t r = threadIdx.x; r <= ns; r += kThreads) {
-        const uint64_t v = off_at(d, ilo + r);
-        s_rel[r] = v <= t0 ? 0u : uint32_t(min(v - t0, uint64_t(kWriteTile)));
-      }
-      for (uint32_t r = threadIdx.x; r < ns; r += kThreads) s_beg[r] = d.pbeg[ilo + r];
-      if (threadIdx.x == 0) s_skip = uint32_t(t0 - off_at(d, ilo));  // rows of probe row ilo before this tile
-      __syncthreads();
-      if (q0 < n) {
-        uint32_t r = upper_bound_u32(s_rel, 0, ns + 1, q0) - 1;
-        const uint32_t skip = s_skip;
-#pragma unroll 4
-        for (int j = 0; j < kWriteRows; ++j) {
-          const uint32_t q = q0 + j;
-          if (q >= n) break;
-          if (s_rel[r + 1] <= q) {
-            ++r;
-            if (s_rel[r + 1] <= q) r = upper_bound_u32(s_rel, r + 1, ns + 1, q) - 1;
-          }
-          s_pk[mi(q)] = r;
-          s_bk[mi(q)] = s_beg[r] + (q - s_rel[r]) + (r == 0 ? skip : 0u);
-        }
-      }
-    } else if (q0 < n) {
-      // more probe rows than the stage holds (rows with few matches): global search
-      const uint64_t hi = ilo + nst + 1;
-      uint64_t i = row_of(d, t0 + q0, ilo, hi);
+    // Up to kStageChunks * kStageRows feeding rows pass through the stage in
+    // chunks; each chunk maps the output rows that fall in its rows' ranges.
+    // More feeding rows than that (most of them without a match) are searched
+    // in global memory instead.
+    const bool staged = ihi - ilo <= uint64_t(kStageChunks) * kStageRows;
+    if (!staged && q0 < n) {
+      uint64_t i = row_of(d, t0 + q0, ilo, ihi + 1);
       for (int j = 0; j < kWriteRows; ++j) {
         const uint32_t q = q0 + j;
         if (q >= n) break;
         const uint64_t r = t0 + q;
-        if (off_at(d, i + 1) <= r) i = row_of(d, r, i + 1, hi);
+        if (off_at(d, i + 1) <= r) i = row_of(d, r, i + 1, ihi + 1);
         s_pk[mi(q)] = uint32_t(i - ilo);
         s_bk[mi(q)] = d.pbeg[i] + uint32_t(r - off_at(d, i));
       }
     }
-    __syncthreads();
+    for (uint64_t c0 = ilo; staged && c0 < ihi; c0 += kStageRows) {
+      const uint32_t ns = uint32_t(min(uint64_t(kStageRows), ihi - c0));
+      for (uint32_t r = threadIdx.x; r <= ns; r += kThreads) {
+        const uint64_t v = off_at(d, c0 + r);
+        s_rel[r] = v <= t0 ? 0u : uint32_t(min(v - t0, uint64_t(kWriteTile)));
+      }
+      for (uint32_t r = threadIdx.x; r < ns; r += kThreads) s_beg[r] = d.pbeg[c0 + r];
+      if (threadIdx.x == 0 && c0 == ilo) s_skip = uint32_t(t0 - off_at(d, ilo));  // rows of ilo before this tile
+      __syncthreads();
+      const uint32_t qa = max(q0, s_rel[0]), qb = min(q0 + kWriteRows, min(s_rel[ns], n));
+      if (qa < qb) {
+        uint32_t r = upper_bound_u32(s_rel, 0, ns + 1, qa) - 1;
+        const uint32_t skip = c0 == ilo ? s_skip : 0u, rbase = uint32_t(c0 - ilo);
+        for (uint32_t q = qa; q < qb; ++q) {
+          if (s_rel[r + 1] <= q) {
+            ++r;
+            if (s_rel[r + 1] <= q) r = upper_bound_u32(s_rel, r + 1, ns + 1, q) - 1;
+          }
+          s_pk[mi(q)] = rbase + r;
+          s_bk[mi(q)] = s_beg[r] + (q - s_rel[r]) + (r == 0 ? skip : 0u);
+        }
+      }
+      __syncthreads();
+    }
+    if (!staged) __syncthreads();
     // probe-side columns, then build-side columns: one index array live at a time
     for (int side = 0; side < 2; ++side) {
       const uint32_t* s_map = side ? s_bk : s_pk;
       uint32_t idx[kWriteRows];
 #pragma unroll
-      for (int j = 0; j < kWriteRows; ++j) {
-        const uint32_t q = uint32_t(j) * kThreads + threadIdx.x;
-        idx[j] = q < n ? s_map[mi(q)] : 0u;
+      for (int i = 0; i < kWriteRows; ++i) {
+        const uint32_t q = run_row(i);
+        idx[i] = q < n ? s_map[mi(q)] : 0u;
       }
       const uint32_t st = side ? uint32_t(d.nbv) : 1u;
+      if (side && d.nbv == 2) {
+        // both build columns from one 8-byte gather per row
+        int c0 = -1, c1 = -1;
+        for (int c = 0; c < d.ncols; ++c)
+          if ((d.from_build >> c) & 1u) (d.src[c] == d.grouped ? c0 : c1) = c;
+        if (n == kWriteTile) write_pair<true>(d.grouped, idx, d.out[c0] + t0, d.out[c1] + t0, n);
+        else write_pair<false>(d.grouped, idx, d.out[c0] + t0, d.out[c1] + t0, n);
+        continue;
+      }
       for (int c = 0; c < d.ncols; ++c) {
         if (int((d.from_build >> c) & 1u) != side) continue;
         const uint32_t* src = side ? d.src[c] : d.src[c] + ilo;
