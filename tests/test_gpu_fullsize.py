@@ -66,3 +66,98 @@ def test_skewed_join_full_size():
                 return out.vars, [np.ascontiguousarray(got_rows[:, c]) for c in range(6)]
 
         assert_same_multiset(Rows, oracle.join_mapreduce(As, Bs), "sampled keys")
+
+
+def test_uneven_batch_full_size():
+    """The 256-join batch at full size through mapsq_join_batch: every join's row
+    count against the cardinality identity from independent histograms; joins of
+    up to 2^18 rows in full against the oracle, larger ones on a sample of keys
+    (the hottest key of the left side included)."""
+    import torch
+    from paper_1702_03484_gb300 import Context
+    joins = gen.uneven_batch(seed=4)
+    r = gen.Rng(41)
+    with Context(device=0) as ctx:
+        dev = [(ctx.table(L.vars, [torch.from_numpy(c).cuda() for c in L.cols]),
+                ctx.table(R.vars, [torch.from_numpy(c).cuda() for c in R.cols])) for L, R, _ in joins]
+        outs = ctx.join_batch([a for a, _ in dev], [b for _, b in dev])
+        assert len(outs) == len(joins)
+        for j, ((L, R, s), out) in enumerate(zip(joins, outs)):
+            kl, cl = np.unique(L.cols[0], return_counts=True)
+            kr, cr = np.unique(R.cols[0], return_counts=True)
+            _, il, ir = np.intersect1d(kl, kr, assume_unique=True, return_indices=True)
+            assert out.nrows == int((cl[il].astype(np.int64) * cr[ir]).sum()), f"join {j} (s={s})"
+            if out.nrows <= 1 << 18:
+                assert_same_multiset(out, oracle.join_mapreduce(L, R), f"join {j}")
+            else:
+                common = kl[il]
+                sample = np.unique(np.concatenate((kl[np.argsort(-cl)[:1]], common[r.below(6, common.shape[0])])))
+                key_col = out.device_columns()[out.vars.index(0)]
+                sel = torch.isin(key_col.view(torch.int32), torch.from_numpy(sample.view(np.int32)).cuda())
+                got = torch.stack([c.view(torch.int32)[sel] for c in out.device_columns()], dim=1)
+                got = got.cpu().numpy().view(np.uint32)
+                Ls = gen.Table(L.vars, [c[np.isin(L.cols[0], sample)] for c in L.cols])
+                Rs = gen.Table(R.vars, [c[np.isin(R.cols[0], sample)] for c in R.cols])
+
+                class Rows:
+                    nrows = got.shape[0]
+
+                    @staticmethod
+                    def to_host():
+                        return out.vars, [np.ascontiguousarray(got[:, c]) for c in range(got.shape[1])]
+
+                assert_same_multiset(Rows, oracle.join_mapreduce(Ls, Rs), f"join {j}, sampled keys")
+            out.free()
+
+
+def test_served_stream_full_size():
+    """Serving over the 1e8-triple graph: a burst of the Poisson stream's queries
+    is served concurrently; every result equals the same query evaluated alone
+    through mapsq_query, and a sample of the smaller ones equals the oracle."""
+    import time
+    from paper_1702_03484_gb300 import Context
+    from gen.bgp import GraphIndex, generate_bgps
+    from gpu_helpers import host_rows
+    s, p, o = gen.university_graph(100_000_000, seed=2)
+    bgps = [b["patterns"] for b in generate_bgps(GraphIndex(s, p, o), 256, seed=5, k_range=(3, 8),
+                                                 var_range=None)]
+    r = gen.Rng(5, 7)
+    stream = [bgps[int(i)] for i in r.below(400, len(bgps))]
+    with Context(device=0) as ctx:
+        ctx.load_triples(s, p, o)
+        ctx.serve_start(max_active=256, mem_budget_bytes=40 << 30)
+        tickets = []
+        for b in stream:
+            tickets.append(ctx.submit(b))
+            time.sleep(0.0005)  # 2000 queries/s
+        served = [None] * len(stream)
+        deadline = time.time() + 300
+        while any(x is None for x in served) and time.time() < deadline:
+            for i, t in enumerate(tickets):
+                if served[i] is None:
+                    res = ctx.poll(t)
+                    if res is not None:
+                        served[i] = oracle.canonical(host_rows(res))
+                        res.free()
+            time.sleep(0.001)
+        stats = ctx.serve_stats()
+        ctx.serve_stop()
+        assert all(x is not None for x in served)
+        assert stats["completed"] == len(stream) and stats["failed"] == 0
+        alone = {}
+        for i, b in enumerate(stream):
+            key = str(b)
+            if key not in alone:
+                res = ctx.query(b)
+                alone[key] = (oracle.canonical(host_rows(res)), res.nrows)
+                res.free()
+            want = alone[key][0]
+            assert served[i][0] == want[0] and np.array_equal(served[i][1], want[1]), b
+    G = oracle.distinct_triples(s, p, o)
+    small = sorted((k for k in alone if alone[k][1] > 0), key=lambda k: alone[k][1])[:4]
+    assert small
+    for key in small:
+        b = next(x for x in stream if str(x) == key)
+        want = oracle.canonical(oracle.evaluate_bgp(G, b, is_set=True))
+        got = alone[key][0]
+        assert got[0] == want[0] and np.array_equal(got[1], want[1]), b
