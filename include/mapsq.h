@@ -91,13 +91,20 @@ typedef struct {
 
 /* A binding table (structure of arrays), see "Tables" above.  A table with
  * ncols == 0 is a set of empty bindings: nrows is 0 (no solution) or 1 (the
- * pattern held, no variable bound). */
+ * pattern held, no variable bound).  Bit c of ``sorted_mask`` says that column
+ * c is in nondecreasing order: scan results carry it (a run of the store is
+ * sorted, Section 2's partial matches come from a sorted index here), and a
+ * join whose key is such a column may use it as the grouped side instead of a
+ * hash table (the Sort step of Algorithm 1, already done).  Zero is always
+ * correct; a caller filling its own table must not set a bit for a column
+ * that is not sorted. */
 typedef struct {
   uint64_t nrows;
   uint32_t ncols;
   int32_t var[MAPSQ_MAX_VARS];
   uint32_t* col[MAPSQ_MAX_VARS];
   int32_t on_device;
+  uint32_t sorted_mask;
 } mapsq_table;
 
 /* Join options; a NULL pointer or zero fields choose defaults. */

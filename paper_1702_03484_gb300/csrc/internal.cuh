@@ -34,6 +34,7 @@ enum KernelId {
   K_COPY,
   K_HLL,
   K_PARTITION,
+  K_SORTED_COUNT,
   K_COUNT_KERNELS
 };
 
@@ -209,7 +210,13 @@ struct PatternRange {
 };
 int validate_pattern(Ctx* ctx, const mapsq_pattern& tp);
 int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* out);
-int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImpl** out);
+// ``key_var``: the variable the result will be joined on (or -1); a pattern
+// with two variables is returned in the store order sorted by it.
+int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImpl** out, int32_t key_var = -1);
+// Columns of ``t`` reordered by ascending variable id (sorted_mask follows).
+void canonical_columns(mapsq_table* t);
+// The one variable that table ``t`` shares with pattern ``tp``, or -1 (none or two).
+int32_t shared_var(const mapsq_table& t, const mapsq_pattern& tp);
 
 // Join (join.cu): k independent joins in one batch of launches.
 int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,

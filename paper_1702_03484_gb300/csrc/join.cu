@@ -53,9 +53,11 @@ constexpr int kHllBits = 12;
 constexpr int kHllRegs = 1 << kHllBits;
 constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides size the table by rows
 constexpr int kBucket = 4;
-constexpr int kPhases = 8;
+constexpr int kPhases = 9;
+constexpr int kSamples = 2048;                         // sorted key column samples per count CTA
+constexpr uint64_t kSortedRatio = 4;                   // sorted side at least this many times the other's rows
 
-enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS };
+enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS, PH_SORTED };
 
 // Open-addressing table of the build side's distinct keys: ``keys`` holds M
 // 64-bit keys in buckets of 4 (one 32-byte sector), probed bucket after bucket
@@ -99,6 +101,8 @@ struct JoinDesc {
   int ncols;
   int cross;                      // no shared variable: output row r pairs probe row r / nb with build row r % nb
   int hash;                       // shared variables and both sides non-empty: the hash path runs
+  int sorted;                     // the build side is sorted on its (one) key column: groups are its runs
+  uint32_t bstride;               // words between a build row's values: nbv (grouped) or 1 (columns)
 };
 
 // Item offsets of one phase: join j owns items [first[j], first[j + 1]).
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(1024) tiles_scan_kernel(JoinDesc* __restrict__
   __shared__ uint64_t s_warp[32];
   __shared__ uint64_t s_carry;
   JoinDesc& d = jd[blockIdx.x];
-  if (!d.hash) {
+  if (!d.hash && !(d.sorted && which == 1)) {
     if (which == 1 && threadIdx.x == 0) totals_out[blockIdx.x] = d.cross ? d.np * d.nb : 0;
     return;
   }
@@ -445,6 +449,85 @@ __global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc
       if (row < np) __stcs(d.pbeg + row, g.x ? group_begin(t, s[q], g.y) : 0u);
       s_cnt[pad(loc)] = g.x;
     }
+  }
+  __syncthreads();
+  uint32_t v[kRowItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    v[q] = s_cnt[pad(threadIdx.x * kRowItems + q)];
+    sum += v[q];
+  }
+  uint64_t tile_sum;
+  uint64_t run = block_scan(sum, s_warp, &tile_sum);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    s_cnt[pad(threadIdx.x * kRowItems + q)] = uint32_t(run);
+    run += v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    const int loc = q * kThreads + threadIdx.x;
+    if (base + loc < np) __stcs(d.local + base + loc, s_cnt[pad(loc)]);
+  }
+  if (threadIdx.x == 0) {
+    d.tile_total[tile] = tile_sum;
+    if (tile_sum > 0xffffffffull) atomicOr(status, 4u);  // tile-local offsets would not fit in 32 bits
+  }
+}
+
+// Count phase of a sorted join.  The build side's key column is sorted, so a
+// key's group is the run of equal keys: every probe row finds its run by two
+// searches (first position >= key, first position > key), narrowed first in
+// kSamples evenly spaced samples of the column held in shared memory, then in
+// global memory between two neighbouring samples.  Counts, group starts and
+// tile-local offsets are then written as in the hash count phase.
+__device__ __forceinline__ uint64_t sample_pos(uint32_t i, uint64_t n) { return uint64_t(i) * n / kSamples; }
+
+__device__ __forceinline__ uint64_t sorted_bound(const uint32_t* __restrict__ x, uint64_t n,
+                                                 const uint32_t* s_key, uint32_t v, bool upper) {
+  uint32_t a = 0, b = kSamples;  // first sample past v
+  while (a < b) {
+    const uint32_t m = (a + b) >> 1;
+    if (upper ? s_key[m] <= v : s_key[m] < v) a = m + 1; else b = m;
+  }
+  uint64_t lo = a ? sample_pos(a - 1, n) + 1 : 0, hi = a < kSamples ? sample_pos(a, n) : n;
+  while (lo < hi) {
+    const uint64_t m = lo + (hi - lo) / 2;
+    const uint32_t xm = __ldg(x + m);
+    if (upper ? xm <= v : xm < v) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) sorted_count_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                               uint32_t k, uint32_t* __restrict__ status) {
+  __shared__ uint32_t s_key[kSamples];
+  __shared__ uint32_t s_cnt[kRowTile + kRowTile / 32];
+  __shared__ uint64_t s_warp[kThreads / 32];
+  const uint32_t jj = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[jj];
+  const uint64_t tile = blockIdx.x - first[jj];
+  const uint64_t base = tile * kRowTile, np = d.np, nx = d.nb;
+  const uint32_t* __restrict__ x = d.bk.c0;
+  auto pad = [](int i) { return i + (i >> 5); };
+  for (int i = threadIdx.x; i < kSamples; i += kThreads) s_key[i] = __ldg(x + sample_pos(uint32_t(i), nx));
+  __syncthreads();
+#pragma unroll 2
+  for (int it = 0; it < kRowItems; ++it) {
+    const int loc = it * kThreads + threadIdx.x;
+    const uint64_t row = base + loc;
+    uint32_t cnt = 0;
+    if (row < np) {
+      const uint32_t v = __ldcs(d.pk.c0 + row);
+      const uint64_t lo = sorted_bound(x, nx, s_key, v, false);
+      const uint64_t hi = lo < nx && __ldg(x + lo) == v ? sorted_bound(x, nx, s_key, v, true) : lo;
+      cnt = uint32_t(hi - lo);
+      __stcs(d.pbeg + row, cnt ? uint32_t(lo) : 0u);
+    }
+    s_cnt[pad(loc)] = cnt;
   }
   __syncthreads();
   uint32_t v[kRowItems];
@@ -676,8 +759,8 @@ __global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc*
         const uint32_t q = run_row(i);
         idx[i] = q < n ? s_map[mi(q)] : 0u;
       }
-      const uint32_t st = side ? uint32_t(d.nbv) : 1u;
-      if (side && d.nbv == 2) {
+      const uint32_t st = side ? d.bstride : 1u;
+      if (side && d.grouped && d.nbv == 2) {
         // both build columns from one 8-byte gather per row
         int c0 = -1, c1 = -1;
         for (int c = 0; c < d.ncols; ++c)
@@ -783,7 +866,7 @@ struct JoinPlan {
   int bside = 1;
   const int *bkey = nullptr, *pkey = nullptr;
   uint64_t nb = 0, np = 0, T = 0, M = 0;
-  bool cross = false, hash = false, hll = false;
+  bool cross = false, hash = false, hll = false, sorted = false;
 };
 
 // A batch of k joins, split in two halves so that the caller can allocate the
@@ -850,7 +933,19 @@ struct BatchJoin {
       MQ_TRY(check_table(ctx, L[j], "left"));
       MQ_TRY(check_table(ctx, R[j], "right"));
       MQ_TRY(make_layout(ctx, L[j], R[j], &pl.lay));
-      const bool build_left = L[j]->nrows < R[j]->nrows;  // build on the smaller side
+      // build on the smaller side; but a side sorted on the (one) key column that
+      // is several times larger than the other is already grouped: it becomes
+      // the build side of a sorted join and the other side searches it
+      const bool lsorted = pl.lay.nkey == 1 && ((L[j]->sorted_mask >> pl.lay.lkey[0]) & 1u);
+      const bool rsorted = pl.lay.nkey == 1 && ((R[j]->sorted_mask >> pl.lay.rkey[0]) & 1u);
+      bool build_left = L[j]->nrows < R[j]->nrows;
+      if (lsorted && L[j]->nrows >= kSortedRatio * R[j]->nrows && R[j]->nrows > 0) {
+        build_left = true;
+        pl.sorted = true;
+      } else if (rsorted && R[j]->nrows >= kSortedRatio * L[j]->nrows && L[j]->nrows > 0) {
+        build_left = false;
+        pl.sorted = true;
+      }
       pl.B = build_left ? L[j] : R[j];
       pl.P = build_left ? R[j] : L[j];
       pl.bside = build_left ? 0 : 1;
@@ -859,7 +954,7 @@ struct BatchJoin {
       pl.nb = pl.B->nrows;
       pl.np = pl.P->nrows;
       pl.cross = pl.lay.nkey == 0;
-      pl.hash = !pl.cross && pl.nb > 0 && pl.np > 0;
+      pl.hash = !pl.cross && pl.nb > 0 && pl.np > 0 && !pl.sorted;
       pl.hll = pl.hash && pl.nb >= kHllMinBuild;
       if (pl.nb >= (uint64_t(1) << 31)) return fail(MAPSQ_ERR_UNSUPPORTED, "build side of 2^31 rows or more");
       if (pl.cross && pl.nb && pl.np > UINT64_MAX / pl.nb) return fail(MAPSQ_ERR_BUDGET, "cross product overflows 64 bits");
@@ -868,6 +963,7 @@ struct BatchJoin {
       d.np = pl.np;
       d.cross = pl.cross;
       d.hash = pl.hash;
+      d.sorted = pl.sorted;
       if (!pl.cross) {
         d.bk = KeyCols{pl.B->col[pl.bkey[0]], pl.lay.nkey == 2 ? pl.B->col[pl.bkey[1]] : nullptr};
         d.pk = KeyCols{pl.P->col[pl.pkey[0]], pl.lay.nkey == 2 ? pl.P->col[pl.pkey[1]] : nullptr};
@@ -952,11 +1048,20 @@ struct BatchJoin {
     MQ_TRY(mem->get(std::max<size_t>(groups, 1), &all_groups));
     if (keys) MQ_TRY(cuda(cudaMemsetAsync(all_keys, 0xff, keys * 8, stream), "memset"));  // all slots empty
     if (groups) MQ_TRY(cuda(cudaMemsetAsync(all_groups, 0, groups * 8, stream), "memset"));
-    std::vector<uint64_t> ins(k, 0), slots(k, 0), scat(k, 0), cnt(k, 0);
+    std::vector<uint64_t> ins(k, 0), slots(k, 0), scat(k, 0), cnt(k, 0), scnt(k, 0);
     size_t ko = 0, go = 0;
     for (uint32_t j = 0; j < k; ++j) {
       const JoinPlan& pl = plans[j];
       JoinDesc& d = descs[j];
+      if (pl.sorted) {
+        const uint64_t nt = ceil_div(pl.np, kRowTile);
+        MQ_TRY(mem->get(pl.np, &d.local));
+        MQ_TRY(mem->get(pl.np, &d.pbeg));
+        MQ_TRY(mem->get(nt, &d.tile_total));
+        MQ_TRY(mem->get(nt + 1, &d.tile_base));
+        scnt[j] = nt;
+        continue;
+      }
       if (!pl.hash) continue;
       d.t.keys = all_keys + ko;
       d.t.group = all_groups + go;
@@ -983,47 +1088,57 @@ struct BatchJoin {
     set_items(PH_SLOTS, slots);
     set_items(PH_SCATTER, scat);
     set_items(PH_COUNT, cnt);
+    set_items(PH_SORTED, scnt);
     return MAPSQ_OK;
   }
 
   int count_phases(uint64_t* totals) {
     MQ_TRY(upload_descs());
     double bytes = 0;
-    int r = rec(K_HASH_INSERT);
     if (items(PH_INSERT)) {
+      for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.nb : 0;
+      const int r = rec(K_HASH_INSERT);
       hash_insert_kernel<<<unsigned(items(PH_INSERT)), kThreads, 0, stream>>>(d_descs, phase_first(PH_INSERT), k,
                                                                                status);
       launched();
+      done(r, bytes);
     }
-    for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.nb : 0;
-    done(r, bytes);
-    r = rec(K_PREFIX_SUM);
     if (items(PH_SLOTS)) {
+      bytes = 0;
+      for (auto& pl : plans) bytes += pl.hash ? 16.0 * (pl.M + 1) : 0;
+      const int r = rec(K_PREFIX_SUM);
       slot_scan_kernel<<<unsigned(items(PH_SLOTS)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SLOTS), k);
       launched();
       tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 0, nullptr);
       launched();
+      done(r, bytes);
     }
-    bytes = 0;
-    for (auto& pl : plans) bytes += pl.hash ? 16.0 * (pl.M + 1) : 0;
-    done(r, bytes);
-    r = rec(K_HASH_SCATTER);
     if (items(PH_SCATTER)) {
+      bytes = 0;
+      for (uint32_t j = 0; j < k; ++j) bytes += plans[j].hash ? 4.0 * descs[j].nbv * plans[j].nb : 0;
+      const int r = rec(K_HASH_SCATTER);
       hash_scatter_kernel<<<unsigned(items(PH_SCATTER)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SCATTER), k);
       launched();
+      done(r, bytes);
     }
-    bytes = 0;
-    for (uint32_t j = 0; j < k; ++j) bytes += plans[j].hash ? 4.0 * descs[j].nbv * plans[j].nb : 0;
-    done(r, bytes);
-    r = rec(K_PROBE_COUNT);
     if (items(PH_COUNT)) {
+      bytes = 0;
+      for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.np : 0;
+      const int r = rec(K_PROBE_COUNT);
       probe_count_kernel<<<unsigned(items(PH_COUNT)), kThreads, 0, stream>>>(d_descs, phase_first(PH_COUNT), k,
                                                                              status);
       launched();
+      done(r, bytes);
     }
-    bytes = 0;
-    for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.np : 0;
-    done(r, bytes);
+    if (items(PH_SORTED)) {
+      bytes = 0;
+      for (auto& pl : plans) bytes += pl.sorted ? 4.0 * pl.np : 0;
+      const int r = rec(K_SORTED_COUNT);
+      sorted_count_kernel<<<unsigned(items(PH_SORTED)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SORTED), k,
+                                                                               status);
+      launched();
+      done(r, bytes);
+    }
     tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 1, totals);
     launched();
     return cuda(cudaGetLastError(), "count phases");
@@ -1064,15 +1179,16 @@ struct BatchJoin {
       JoinDesc& d = descs[j];
       d.ncols = pl.lay.ncols;
       d.from_build = 0;
+      d.bstride = pl.sorted ? 1u : uint32_t(d.nbv);
       uint32_t b = 0;
       double in = 0;
       for (int c = 0; c < pl.lay.ncols; ++c) {
         const bool fb = pl.lay.side[c] == pl.bside && c >= pl.lay.nkey;
         d.out[c] = out[j] ? out[j][c] : nullptr;  // joins not taken have no output table
         if (fb) {
-          d.src[c] = pl.cross ? pl.B->col[pl.lay.col[c]] : d.grouped + b++;
+          d.src[c] = pl.cross || pl.sorted ? pl.B->col[pl.lay.col[c]] : d.grouped + b++;
           d.from_build |= 1u << c;
-          in += 4.0 * pl.nb;
+          in += 4.0 * (pl.sorted ? std::min(pl.nb, pl.T) : pl.nb);  // a sorted side is read where it matches
         } else {
           // key columns and the probe side's own columns come from the probe row
           d.src[c] = pl.P->col[c < pl.lay.nkey ? pl.pkey[c] : pl.lay.col[c]];

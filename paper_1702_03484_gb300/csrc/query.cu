@@ -22,16 +22,31 @@ uint32_t pattern_var_set(const mapsq_pattern& tp) {
 
 // Permute the columns of a result so that its variables are in ascending id
 // (a pointer permutation: no data moves).
+}  // namespace
+
 void canonical_columns(mapsq_table* t) {
   const uint32_t n = t->ncols;
   for (uint32_t i = 1; i < n; ++i)
     for (uint32_t j = i; j > 0 && t->var[j - 1] > t->var[j]; --j) {
       std::swap(t->var[j - 1], t->var[j]);
       std::swap(t->col[j - 1], t->col[j]);
+      const uint32_t a = (t->sorted_mask >> (j - 1)) & 1u, b = (t->sorted_mask >> j) & 1u;
+      t->sorted_mask = (t->sorted_mask & ~(3u << (j - 1))) | (b << (j - 1)) | (a << j);
     }
 }
 
-}  // namespace
+int32_t shared_var(const mapsq_table& t, const mapsq_pattern& tp) {
+  int32_t found = -1;
+  int n = 0;
+  for (uint32_t c = 0; c < t.ncols; ++c) {
+    const int32_t v = t.var[c];
+    if (((tp.var_mask & MAPSQ_VAR_S) && int32_t(tp.s) == v) || ((tp.var_mask & MAPSQ_VAR_O) && int32_t(tp.o) == v)) {
+      found = v;
+      ++n;
+    }
+  }
+  return n == 1 ? found : -1;
+}
 
 // Greedy order: the pattern with the fewest matches first, then repeatedly the
 // one with the fewest matches among those sharing a variable with the patterns
@@ -97,7 +112,7 @@ int query_batch(Ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const u
       if (l >= ns[q]) continue;
       const uint32_t pi = order[q][l];
       TableImpl* part = nullptr;
-      rc = scan_emit(ctx, bgps[q][pi], ranges[off[q] + pi], &part);
+      rc = scan_emit(ctx, bgps[q][pi], ranges[off[q] + pi], &part, shared_var(acc[q]->pub, bgps[q][pi]));
       if (rc != MAPSQ_OK) break;
       who.push_back(q);
       parts.push_back(part);

@@ -176,7 +176,7 @@ int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* ou
   return MAPSQ_OK;
 }
 
-int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImpl** out) {
+int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImpl** out, int32_t key_var) {
   const Store& st = ctx->store;
   int32_t vars[2];
   uint32_t nv = 0;
@@ -192,19 +192,26 @@ int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImp
       MQ_TRY(table_alloc(ctx, rows, 0, vars, &t));
       break;
     // a run of the store is already the partial-match table: a view, no copy
+    // (the run's remaining column is sorted: o within (p, s), s within (p, o))
     case KIND_S_BOUND: {
       uint32_t* cols[1] = {st.so_o + r.lo};
       MQ_TRY(table_view(ctx, rows, 1, vars, cols, st.shared, &t));
+      t->pub.sorted_mask = 1u;
       break;
     }
     case KIND_O_BOUND: {
       uint32_t* cols[1] = {st.os_s + r.lo};
       MQ_TRY(table_view(ctx, rows, 1, vars, cols, st.shared, &t));
+      t->pub.sorted_mask = 1u;
       break;
     }
+    // the predicate's whole segment: the (p, s, o) order is sorted by s, the
+    // (p, o, s) order by o; the join key decides which one is returned
     case KIND_TWO_VARS: {
-      uint32_t* cols[2] = {st.so_s + r.lo, st.so_o + r.lo};
+      const bool by_o = key_var >= 0 && key_var == int32_t(tp.o);
+      uint32_t* cols[2] = {by_o ? st.os_s + r.lo : st.so_s + r.lo, by_o ? st.os_o + r.lo : st.so_o + r.lo};
       MQ_TRY(table_view(ctx, rows, 2, vars, cols, st.shared, &t));
+      t->pub.sorted_mask = by_o ? 2u : 1u;
       break;
     }
     case KIND_SAME_VAR: {
@@ -214,17 +221,24 @@ int scan_emit(Ctx* ctx, const mapsq_pattern& tp, const PatternRange& r, TableImp
       MQ_TRY(scratch.get(rows + 1, &flag));
       MQ_TRY(scratch.get(rows + 1, &pos));
       unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(ceil_div(rows, 256), 152ull * 16)));
-      int rec = prof_begin(ctx, K_SCAN_FILTER);
-      if (rows) { same_var_flags_kernel<<<grid, 256, 0, ctx->stream>>>(st.so_s + r.lo, st.so_o + r.lo, rows, flag); ++ctx->launches; }
-      prof_end(ctx, rec, double(rows) * 12);
+      if (rows) {
+        const int rec = prof_begin(ctx, K_SCAN_FILTER);
+        same_var_flags_kernel<<<grid, 256, 0, ctx->stream>>>(st.so_s + r.lo, st.so_o + r.lo, rows, flag);
+        ++ctx->launches;
+        prof_end(ctx, rec, double(rows) * 12);
+      }
       MQ_TRY(prefix_sum_u32_u64(ctx, flag, pos, rows));
       uint64_t m = 0;
       MQ_TRY(read_u64(ctx, pos + rows, &m, 1));
       MQ_TRY(table_alloc(ctx, m, 1, vars, &t));
-      rec = prof_begin(ctx, K_SCAN_FILTER);
-      if (rows) { same_var_compact_kernel<<<grid, 256, 0, ctx->stream>>>(st.so_s + r.lo, rows, flag, pos, t->pub.col[0]); ++ctx->launches; }
-      prof_end(ctx, rec, double(rows) * 8 + double(m) * 4);
+      if (rows) {
+        const int rec = prof_begin(ctx, K_SCAN_FILTER);
+        same_var_compact_kernel<<<grid, 256, 0, ctx->stream>>>(st.so_s + r.lo, rows, flag, pos, t->pub.col[0]);
+        ++ctx->launches;
+        prof_end(ctx, rec, double(rows) * 8 + double(m) * 4);
+      }
       MQ_CUDA(cudaGetLastError());
+      t->pub.sorted_mask = 1u;  // kept in the (p, s, o) order
       break;
     }
     default:

@@ -47,14 +47,6 @@ struct Done {
 
 uint64_t table_bytes(const TableImpl* t) { return t ? t->bytes : 0; }
 
-void canonical_columns(mapsq_table* t) {
-  const uint32_t n = t->ncols;
-  for (uint32_t i = 1; i < n; ++i)
-    for (uint32_t j = i; j > 0 && t->var[j - 1] > t->var[j]; --j) {
-      std::swap(t->var[j - 1], t->var[j]);
-      std::swap(t->col[j - 1], t->col[j]);
-    }
-}
 
 }  // namespace
 
@@ -141,7 +133,7 @@ struct Server {
       if (q->joined >= q->bgp.size()) continue;
       const uint32_t pi = q->order[q->joined];
       TableImpl* part = nullptr;
-      q->status = scan_emit(ctx, q->bgp[pi], q->ranges[pi], &part);
+      q->status = scan_emit(ctx, q->bgp[pi], q->ranges[pi], &part, shared_var(q->acc->pub, q->bgp[pi]));
       if (q->status != MAPSQ_OK) continue;
       who.push_back(q);
       parts.push_back(part);

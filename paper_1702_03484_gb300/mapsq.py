@@ -40,7 +40,7 @@ class Pattern(C.Structure):
 
 class Table(C.Structure):
     _fields_ = [("nrows", C.c_uint64), ("ncols", C.c_uint32), ("var", C.c_int32 * MAX_VARS),
-                ("col", C.c_void_p * MAX_VARS), ("on_device", C.c_int32)]
+                ("col", C.c_void_p * MAX_VARS), ("on_device", C.c_int32), ("sorted_mask", C.c_uint32)]
 
 
 class JoinOpts(C.Structure):
@@ -339,9 +339,12 @@ def mapsq_serve_stop(ctx):
     _check(ctx, lib().mapsq_serve_stop(ctx))
 
 
-def table_view(vars_, cols, nrows=None):
-    """A ``Table`` struct describing caller-owned device columns (no copy)."""
+def table_view(vars_, cols, nrows=None, sorted_cols=()):
+    """A ``Table`` struct describing caller-owned device columns (no copy);
+    ``sorted_cols`` lists the columns the caller knows to be nondecreasing."""
     t = Table()
+    for c in sorted_cols:
+        t.sorted_mask |= 1 << c
     t.nrows = int(cols[0].shape[0]) if cols else int(nrows or 0)
     t.ncols = len(vars_)
     for c in range(MAX_VARS):

@@ -211,3 +211,57 @@ def test_join_batch_matches_oracle(ctx):
         assert_same_multiset(o, oracle.join_mapreduce(L, R), f"batch item {i}")
         o.free()
     assert ctx.join_batch([], []) == []
+
+
+def _sorted_join(ctx, X, Y, x_left, sorted_col=0):
+    """Join through caller-described tables, X marked sorted on ``sorted_col``."""
+    import ctypes as C
+    import torch
+    from paper_1702_03484_gb300 import TableRef, mapsq
+    xc = [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in X.cols]
+    yc = [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in Y.cols]
+    xv = mapsq.table_view(X.vars, xc, X.nrows, sorted_cols=(sorted_col,))
+    yv = mapsq.table_view(Y.vars, yc, Y.nrows)
+    a, b = (xv, yv) if x_left else (yv, xv)
+    before = ctx.kernel_stats().get("sorted_count", {}).get("launches", 0)
+    out = TableRef(ctx, mapsq.mapsq_join(ctx.handle, C.pointer(a), C.pointer(b)))
+    torch.cuda.synchronize()
+    used = ctx.kernel_stats().get("sorted_count", {}).get("launches", 0) > before
+    return out, used
+
+
+def _sorted_table(r, n, vars_, key_col, dom):
+    cols = [r.below(n, dom).astype(np.uint32) for _ in vars_]
+    cols[key_col] = np.sort(cols[key_col])
+    return gen.Table(vars_, cols)
+
+
+def test_sorted_build_side(ctx):
+    """A side sorted on the key column and at least four times the other's rows
+    is used as the grouped side (the sorted join); results equal the oracle,
+    with keys absent, below and above its range, extreme ids and long runs."""
+    ctx.set_profiling(True)
+    try:
+        r = gen.Rng(77)
+        for seed, (nx, ny, dom) in enumerate([(100_000, 1000, 5000), (50, 12, 40), (300_000, 70_000, 1 << 20),
+                                              (4096, 1024, 3)]):
+            X = _sorted_table(r, nx, [3, 0, 9], 1, dom)
+            X.cols[1][:5] = 0
+            X.cols[1][-3:] = 0xFFFFFFFF
+            Y = gen.Table([0, 12], [r.below(ny, dom + 10).astype(np.uint32), r.u32(ny)])
+            Y.cols[0][:3] = [0, 0xFFFFFFFF, dom + 5]
+            want = oracle.join_mapreduce(X, Y)
+            for x_left in (True, False):
+                out, used = _sorted_join(ctx, X, Y, x_left, sorted_col=1)
+                assert used, "sorted join not chosen"
+                assert_same_multiset(out, want if x_left else oracle.join_mapreduce(Y, X), f"case {seed} {x_left}")
+                out.free()
+        # too small a ratio: the hash join runs, same result
+        X = _sorted_table(r, 1000, [0, 5], 0, 300)
+        Y = gen.Table([0, 6], [r.below(800, 300).astype(np.uint32), r.u32(800)])
+        out, used = _sorted_join(ctx, X, Y, True)
+        assert not used
+        assert_same_multiset(out, oracle.join_mapreduce(X, Y), "hash fallback")
+        out.free()
+    finally:
+        ctx.set_profiling(False)
