@@ -580,6 +580,7 @@ def run_ours(args):
 
     with Context(device=local) as ctx:
         w.setup_gpu(ctx)
+        tune = ctx.autotune()  # the hash-vs-sorted choice for this GPU (not timed)
         stream = torch.cuda.current_stream(dev)
         for _ in range(args.warmup - 1):
             w.run_gpu(ctx)
@@ -684,6 +685,9 @@ def run_ours(args):
             "e2e": {"value": e_rows / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d // e_steps,
                     "d2h_bytes_per_step": d2h // e_steps},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(), "other_form": batched,
+            "autotune": {"sorted_ratio": tune["sorted_ratio"],
+                         "points": [(p["ratio"], round(p["hash_ms"], 3), round(p["sorted_ms"], 3))
+                                    for p in tune["points"]]},
             "kernels_last_warmup_step": {k: {"launches": v["launches"], "ms": round(v["device_ms"], 4)}
                                          for k, v in warm_stats.items()}}
     if not args.no_cpu_baseline and world == 1:
@@ -719,6 +723,7 @@ def run_serving(args):
     w = Serving()
     with Context(device=local) as ctx:
         w.setup_gpu(ctx)
+        tune = ctx.autotune()  # the hash-vs-sorted choice for this GPU (not timed)
         # warm-up stream, profiled in full: it names the kernel with the most device time
         ctx.reset_stats()
         ctx.set_profiling(True)
@@ -784,6 +789,7 @@ def run_serving(args):
                     "d2h_bytes_per_step": d2h // e_steps, "p50_ms": e_counters["p50_ms"],
                     "p99_ms": e_counters["p99_ms"]},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(),
+            "autotune": {"sorted_ratio": tune["sorted_ratio"]},
             "kernels_warmup_stream": {k: {"launches": v["launches"], "ms": round(v["device_ms"], 4)}
                                       for k, v in warm_stats.items()}}
     if not args.no_cpu_baseline and world == 1:

@@ -66,9 +66,16 @@ extern "C" {
 #define MAPSQ_VAR_P 2u
 #define MAPSQ_VAR_O 4u
 
-/* Join algorithms for mapsq_join_opts.algorithm. */
+/* Join algorithms for mapsq_join_opts.algorithm.  Both compute Algorithm 1's
+ * result; they differ in how equal keys are brought together (its Sort step):
+ * HASH groups the smaller side by key in a hash table; SORTED uses a side
+ * whose key column is already sorted (sorted_mask) as the groups and searches
+ * it with the other side's keys.  AUTO takes SORTED when a side is sorted on
+ * the (single) key column and at least the context's sorted ratio times the
+ * other side's rows (see mapsq_autotune), else HASH. */
 #define MAPSQ_JOIN_AUTO 0
 #define MAPSQ_JOIN_HASH 1
+#define MAPSQ_JOIN_SORTED 2
 
 typedef struct mapsq_ctx mapsq_ctx;
 
@@ -109,11 +116,31 @@ typedef struct {
 
 /* Join options; a NULL pointer or zero fields choose defaults. */
 typedef struct {
-  int32_t algorithm;     /* MAPSQ_JOIN_AUTO or MAPSQ_JOIN_HASH */
-  int32_t block_threads; /* threads per CTA of the write pass (multiple of 32, <= 1024) */
-  int32_t tile_rows;     /* output rows per CTA tile of the write pass (multiple of 4 * block_threads) */
-  int32_t reserved;
+  int32_t algorithm;     /* MAPSQ_JOIN_AUTO, _HASH or _SORTED (SORTED falls back to HASH when no
+                            side is sorted on a single key column) */
+  int32_t reserved[3];   /* zero */
 } mapsq_join_opts;
+
+/* What mapsq_autotune measured: per tested ratio r of sorted-side rows to
+ * other-side rows, the time of one join by each algorithm. */
+typedef struct {
+  uint32_t sorted_ratio;   /* chosen: AUTO takes SORTED from this ratio up (0xFFFFFFFF = never) */
+  uint32_t points;         /* tested ratios */
+  uint32_t ratio[12];
+  double hash_ms[12];
+  double sorted_ms[12];
+  uint64_t sorted_rows;    /* rows of the sorted side in the test joins */
+} mapsq_autotune_result;
+
+/* Autotune the AUTO choice between the hash and the sorted join on this GPU:
+ * joins a sorted side of ``sorted_rows`` rows (0 = 2^22; keys k / 2, so every
+ * key twice) with other sides of sorted_rows / r rows (keys uniform over the
+ * same range) for r = 1, 2, 4, ..., 2048, timing each algorithm (best of
+ * three, host synchronisation included), and sets the context's sorted ratio
+ * to the smallest r from which SORTED is never slower.  ``out`` may be NULL.
+ * Uses about 40 bytes per sorted row of device memory.  Errors: BUSY
+ * (serving), OOM, BUDGET, CUDA. */
+MAPSQ_API int mapsq_autotune(mapsq_ctx* ctx, uint64_t sorted_rows, mapsq_autotune_result* out);
 
 /* Serving loop options (mapsq_serve_start); zero fields choose defaults. */
 typedef struct {

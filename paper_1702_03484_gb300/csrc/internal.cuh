@@ -121,6 +121,7 @@ struct mapsq_ctx {
   std::vector<cudaEvent_t> free_events;
   mapsq::KernelTotals totals[mapsq::K_COUNT_KERNELS];
   std::vector<mapsq::TableImpl*> live_tables;
+  uint32_t sorted_ratio = 4;      // AUTO joins: sorted side rows / other side rows from which SORTED runs
 };
 
 namespace mapsq {
@@ -146,23 +147,36 @@ int cuda_fail(Ctx* ctx, cudaError_t e, const char* what, const char* file, int l
 int dev_alloc(Ctx* ctx, size_t bytes, void** out);
 void dev_free(Ctx* ctx, void* p, size_t bytes);
 
-// RAII holder for scratch allocations inside one call.
+// RAII holder for scratch allocations inside one call: requests are carved
+// (256-byte aligned) from chunks of at least kChunk bytes, so that a join's
+// dozen small arrays cost one allocation and one free.
 struct Scratch {
+  static constexpr size_t kChunk = size_t(256) << 10;
   Ctx* ctx;
   std::vector<std::pair<void*, size_t>> blocks;
+  char* cur = nullptr;
+  size_t left = 0;
   explicit Scratch(Ctx* c) : ctx(c) {}
   ~Scratch() {
     for (auto& b : blocks) dev_free(ctx, b.first, b.second);
   }
   template <class T>
   int get(size_t count, T** out) {
-    void* p = nullptr;
     size_t bytes = count * sizeof(T);
-    if (bytes == 0) bytes = 16;
-    int rc = dev_alloc(ctx, bytes, &p);
-    if (rc != MAPSQ_OK) return rc;
-    blocks.push_back({p, bytes});
-    *out = static_cast<T*>(p);
+    bytes = ((bytes ? bytes : 16) + 255) & ~size_t(255);
+    if (bytes > left) {
+      void* p = nullptr;
+      size_t chunk = bytes < kChunk ? kChunk : bytes;
+      int rc = dev_alloc(ctx, chunk, &p);
+      if (rc == MAPSQ_ERR_BUDGET && chunk > bytes) rc = dev_alloc(ctx, chunk = bytes, &p);  // just what fits
+      if (rc != MAPSQ_OK) return rc;
+      blocks.push_back({p, chunk});
+      cur = static_cast<char*>(p);
+      left = chunk;
+    }
+    *out = reinterpret_cast<T*>(cur);
+    cur += bytes;
+    left -= bytes;
     return MAPSQ_OK;
   }
 };

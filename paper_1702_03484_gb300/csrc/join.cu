@@ -55,7 +55,9 @@ constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides si
 constexpr int kBucket = 4;
 constexpr int kPhases = 9;
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA
-constexpr uint64_t kSortedRatio = 4;                   // sorted side at least this many times the other's rows
+constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
+constexpr int kSortedItems = kRowTile / kSortedThreads;
+constexpr uint32_t kSortedRatio = 4;                   // default: sorted side at least this many times the other's rows
 
 enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS, PH_SORTED };
 
@@ -186,7 +188,8 @@ __device__ __forceinline__ uint32_t group_begin(const HashTable& t, uint32_t s, 
 // Block-wide exclusive scan of one value per thread (row order = thread order
 // of ``vals`` laid out kRowItems consecutive rows per thread); returns the
 // thread's exclusive prefix and the block total.
-__device__ __forceinline__ uint64_t block_scan(uint64_t sum, uint64_t* s_warp, uint64_t* total) {
+template <int NT>
+__device__ __forceinline__ uint64_t block_scan_n(uint64_t sum, uint64_t* s_warp, uint64_t* total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t inc = sum;
 #pragma unroll
@@ -198,13 +201,17 @@ __device__ __forceinline__ uint64_t block_scan(uint64_t sum, uint64_t* s_warp, u
   __syncthreads();
   uint64_t before = 0, tot = 0;
 #pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) {
+  for (int w = 0; w < NT / 32; ++w) {
     const uint64_t x = s_warp[w];
     if (w < warp) before += x;
     tot += x;
   }
   *total = tot;
   return before + inc - sum;
+}
+
+__device__ __forceinline__ uint64_t block_scan(uint64_t sum, uint64_t* s_warp, uint64_t* total) {
+  return block_scan_n<kThreads>(sum, s_warp, total);
 }
 
 // ------------------------------------------------------------------ phases
@@ -502,22 +509,23 @@ __device__ __forceinline__ uint64_t sorted_bound(const uint32_t* __restrict__ x,
   return lo;
 }
 
-__global__ void __launch_bounds__(kThreads) sorted_count_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
-                                                               uint32_t k, uint32_t* __restrict__ status) {
+__global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const JoinDesc* __restrict__ jd,
+                                                                     const uint64_t* first, uint32_t k,
+                                                                     uint32_t* __restrict__ status) {
   __shared__ uint32_t s_key[kSamples];
   __shared__ uint32_t s_cnt[kRowTile + kRowTile / 32];
-  __shared__ uint64_t s_warp[kThreads / 32];
+  __shared__ uint64_t s_warp[kSortedThreads / 32];
   const uint32_t jj = item_join(first, k, blockIdx.x);
   const JoinDesc& d = jd[jj];
   const uint64_t tile = blockIdx.x - first[jj];
   const uint64_t base = tile * kRowTile, np = d.np, nx = d.nb;
   const uint32_t* __restrict__ x = d.bk.c0;
   auto pad = [](int i) { return i + (i >> 5); };
-  for (int i = threadIdx.x; i < kSamples; i += kThreads) s_key[i] = __ldg(x + sample_pos(uint32_t(i), nx));
+  for (int i = threadIdx.x; i < kSamples; i += kSortedThreads) s_key[i] = __ldg(x + sample_pos(uint32_t(i), nx));
   __syncthreads();
-#pragma unroll 2
-  for (int it = 0; it < kRowItems; ++it) {
-    const int loc = it * kThreads + threadIdx.x;
+#pragma unroll
+  for (int it = 0; it < kSortedItems; ++it) {
+    const int loc = it * kSortedThreads + threadIdx.x;
     const uint64_t row = base + loc;
     uint32_t cnt = 0;
     if (row < np) {
@@ -530,25 +538,25 @@ __global__ void __launch_bounds__(kThreads) sorted_count_kernel(const JoinDesc* 
     s_cnt[pad(loc)] = cnt;
   }
   __syncthreads();
-  uint32_t v[kRowItems];
+  uint32_t v[kSortedItems];
   uint64_t sum = 0;
 #pragma unroll
-  for (int q = 0; q < kRowItems; ++q) {
-    v[q] = s_cnt[pad(threadIdx.x * kRowItems + q)];
+  for (int q = 0; q < kSortedItems; ++q) {
+    v[q] = s_cnt[pad(threadIdx.x * kSortedItems + q)];
     sum += v[q];
   }
   uint64_t tile_sum;
-  uint64_t run = block_scan(sum, s_warp, &tile_sum);
+  uint64_t run = block_scan_n<kSortedThreads>(sum, s_warp, &tile_sum);
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < kRowItems; ++q) {
-    s_cnt[pad(threadIdx.x * kRowItems + q)] = uint32_t(run);
+  for (int q = 0; q < kSortedItems; ++q) {
+    s_cnt[pad(threadIdx.x * kSortedItems + q)] = uint32_t(run);
     run += v[q];
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < kRowItems; ++q) {
-    const int loc = q * kThreads + threadIdx.x;
+  for (int q = 0; q < kSortedItems; ++q) {
+    const int loc = q * kSortedThreads + threadIdx.x;
     if (base + loc < np) __stcs(d.local + base + loc, s_cnt[pad(loc)]);
   }
   if (threadIdx.x == 0) {
@@ -888,6 +896,8 @@ struct BatchJoin {
   std::vector<uint64_t> host;              // read-back buffer
   std::vector<uint8_t> take;               // joins that write() produces (all by default)
   uint32_t k = 0;
+  int algorithm = MAPSQ_JOIN_AUTO;
+  uint32_t sorted_ratio = kSortedRatio;
 
   int fail(int code, const char* what) { return ctx ? set_error(ctx, code, "%s", what) : code; }
   int cuda(cudaError_t e, const char* what) {
@@ -939,11 +949,14 @@ struct BatchJoin {
       const bool lsorted = pl.lay.nkey == 1 && ((L[j]->sorted_mask >> pl.lay.lkey[0]) & 1u);
       const bool rsorted = pl.lay.nkey == 1 && ((R[j]->sorted_mask >> pl.lay.rkey[0]) & 1u);
       bool build_left = L[j]->nrows < R[j]->nrows;
-      if (lsorted && L[j]->nrows >= kSortedRatio * R[j]->nrows && R[j]->nrows > 0) {
-        build_left = true;
-        pl.sorted = true;
-      } else if (rsorted && R[j]->nrows >= kSortedRatio * L[j]->nrows && L[j]->nrows > 0) {
-        build_left = false;
+      const uint64_t nl = L[j]->nrows, nr = R[j]->nrows;
+      const uint64_t ratio = algorithm == MAPSQ_JOIN_SORTED ? 0 : sorted_ratio;
+      const bool allow = algorithm != MAPSQ_JOIN_HASH && ratio != 0xffffffffu && nl > 0 && nr > 0;
+      // both sorted: the larger one is searched
+      const bool use_l = allow && lsorted && nl >= ratio * nr && (!rsorted || nl >= nr);
+      const bool use_r = allow && !use_l && rsorted && nr >= ratio * nl;
+      if (use_l || use_r) {
+        build_left = use_l;
         pl.sorted = true;
       }
       pl.B = build_left ? L[j] : R[j];
@@ -1134,8 +1147,8 @@ struct BatchJoin {
       bytes = 0;
       for (auto& pl : plans) bytes += pl.sorted ? 4.0 * pl.np : 0;
       const int r = rec(K_SORTED_COUNT);
-      sorted_count_kernel<<<unsigned(items(PH_SORTED)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SORTED), k,
-                                                                               status);
+      sorted_count_kernel<<<unsigned(items(PH_SORTED)), kSortedThreads, 0, stream>>>(d_descs, phase_first(PH_SORTED),
+                                                                                     k, status);
       launched();
       done(r, bytes);
     }
@@ -1240,10 +1253,13 @@ struct BatchJoin {
 
 int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
                const mapsq_join_opts* opts, TableImpl** out) {
-  (void)opts;
   if (k == 0) return MAPSQ_OK;
+  if (opts && (opts->algorithm < MAPSQ_JOIN_AUTO || opts->algorithm > MAPSQ_JOIN_SORTED))
+    return set_error(ctx, MAPSQ_ERR_INVALID, "join algorithm %d", opts->algorithm);
   Scratch scratch(ctx);
   BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
+  bj.algorithm = opts ? opts->algorithm : MAPSQ_JOIN_AUTO;
+  bj.sorted_ratio = ctx->sorted_ratio;
   MQ_TRY(bj.prepare(k, L, R));
   MQ_TRY(bj.count());
   std::vector<TableImpl*> tabs(k, nullptr);
@@ -1272,6 +1288,7 @@ int join_batch_admit(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const ma
   if (k == 0) return MAPSQ_OK;
   Scratch scratch(ctx);
   BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
+  bj.sorted_ratio = ctx->sorted_ratio;
   MQ_TRY(bj.prepare(k, L, R));
   MQ_TRY(bj.count());
   // admission in order: result tables are written while they fit in the budget

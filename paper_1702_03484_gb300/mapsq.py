@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libmapsq.so")
 
 MAX_VARS = 16
 VAR_S, VAR_P, VAR_O = 1, 2, 4
-JOIN_AUTO, JOIN_HASH = 0, 1
+JOIN_AUTO, JOIN_HASH, JOIN_SORTED = 0, 1, 2
 
 STATUS = {
     0: "OK", -1: "INVALID", -2: "UNSUPPORTED", -3: "OOM", -4: "BUDGET",
@@ -44,8 +44,12 @@ class Table(C.Structure):
 
 
 class JoinOpts(C.Structure):
-    _fields_ = [("algorithm", C.c_int32), ("block_threads", C.c_int32), ("tile_rows", C.c_int32),
-                ("reserved", C.c_int32)]
+    _fields_ = [("algorithm", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+class AutotuneResult(C.Structure):
+    _fields_ = [("sorted_ratio", C.c_uint32), ("points", C.c_uint32), ("ratio", C.c_uint32 * 12),
+                ("hash_ms", C.c_double * 12), ("sorted_ms", C.c_double * 12), ("sorted_rows", C.c_uint64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -102,6 +106,7 @@ _SIGNATURES = {
     "mapsq_profile_only": (C.c_int, [_P, C.c_char_p]),
     "mapsq_launch_count": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
     "mapsq_join_noalloc": (C.c_int, [_TP, _TP, C.POINTER(_P), C.c_uint64, _TP, C.POINTER(C.c_uint64), _P]),
+    "mapsq_autotune": (C.c_int, [_P, C.c_uint64, C.POINTER(AutotuneResult)]),
     "mapsq_serve_start": (C.c_int, [_P, C.POINTER(ServeOpts)]),
     "mapsq_submit": (C.c_int, [_P, C.POINTER(Pattern), C.c_uint32, C.POINTER(C.c_uint64)]),
     "mapsq_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(_TP)]),
@@ -306,6 +311,14 @@ def mapsq_join_noalloc(left, right, out_cols, capacity, stream=None):
     return rc, out, rows.value
 
 
+def mapsq_autotune(ctx, sorted_rows=0):
+    r = AutotuneResult()
+    _check(ctx, lib().mapsq_autotune(ctx, sorted_rows, C.byref(r)))
+    n = r.points
+    return {"sorted_ratio": r.sorted_ratio, "sorted_rows": r.sorted_rows,
+            "points": [{"ratio": r.ratio[i], "hash_ms": r.hash_ms[i], "sorted_ms": r.sorted_ms[i]} for i in range(n)]}
+
+
 def mapsq_serve_start(ctx, max_active=0, mem_budget_bytes=0):
     opts = ServeOpts(max_active=max_active, mem_budget_bytes=mem_budget_bytes)
     _check(ctx, lib().mapsq_serve_start(ctx, C.byref(opts)))
@@ -468,6 +481,9 @@ class Context:
 
     def launch_count(self):
         return mapsq_launch_count(self.handle)
+
+    def autotune(self, sorted_rows=0):
+        return mapsq_autotune(self.handle, sorted_rows)
 
     def serve_start(self, max_active=0, mem_budget_bytes=0):
         mapsq_serve_start(self.handle, max_active, mem_budget_bytes)

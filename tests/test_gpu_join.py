@@ -213,18 +213,18 @@ def test_join_batch_matches_oracle(ctx):
     assert ctx.join_batch([], []) == []
 
 
-def _sorted_join(ctx, X, Y, x_left, sorted_col=0):
+def _sorted_join(ctx, X, Y, x_left, sorted_col=0, algorithm=0):
     """Join through caller-described tables, X marked sorted on ``sorted_col``."""
     import ctypes as C
     import torch
-    from paper_1702_03484_gb300 import TableRef, mapsq
+    from paper_1702_03484_gb300 import JoinOpts, TableRef, mapsq
     xc = [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in X.cols]
     yc = [torch.from_numpy(np.ascontiguousarray(c)).cuda() for c in Y.cols]
     xv = mapsq.table_view(X.vars, xc, X.nrows, sorted_cols=(sorted_col,))
     yv = mapsq.table_view(Y.vars, yc, Y.nrows)
     a, b = (xv, yv) if x_left else (yv, xv)
     before = ctx.kernel_stats().get("sorted_count", {}).get("launches", 0)
-    out = TableRef(ctx, mapsq.mapsq_join(ctx.handle, C.pointer(a), C.pointer(b)))
+    out = TableRef(ctx, mapsq.mapsq_join(ctx.handle, C.pointer(a), C.pointer(b), JoinOpts(algorithm=algorithm)))
     torch.cuda.synchronize()
     used = ctx.kernel_stats().get("sorted_count", {}).get("launches", 0) > before
     return out, used
@@ -256,12 +256,35 @@ def test_sorted_build_side(ctx):
                 assert used, "sorted join not chosen"
                 assert_same_multiset(out, want if x_left else oracle.join_mapreduce(Y, X), f"case {seed} {x_left}")
                 out.free()
-        # too small a ratio: the hash join runs, same result
+        # too small a ratio: AUTO takes the hash join; SORTED forces the search;
+        # HASH never searches
         X = _sorted_table(r, 1000, [0, 5], 0, 300)
         Y = gen.Table([0, 6], [r.below(800, 300).astype(np.uint32), r.u32(800)])
-        out, used = _sorted_join(ctx, X, Y, True)
+        want = oracle.join_mapreduce(X, Y)
+        for algorithm, expect in ((0, False), (2, True), (1, False)):
+            out, used = _sorted_join(ctx, X, Y, True, algorithm=algorithm)
+            assert used == expect, algorithm
+            assert_same_multiset(out, want, f"algorithm {algorithm}")
+            out.free()
+        X = _sorted_table(r, 40_000, [0, 5], 0, 3000)
+        out, used = _sorted_join(ctx, X, Y, False, algorithm=1)
         assert not used
-        assert_same_multiset(out, oracle.join_mapreduce(X, Y), "hash fallback")
+        assert_same_multiset(out, oracle.join_mapreduce(Y, X), "hash forced")
         out.free()
     finally:
         ctx.set_profiling(False)
+
+
+def test_autotune_sets_ratio_and_joins_stay_exact():
+    from paper_1702_03484_gb300 import Context, MapsqError
+    with Context(device=0) as c:
+        res = c.autotune(sorted_rows=1 << 18)
+        assert res["sorted_rows"] == 1 << 18 and len(res["points"]) == 12
+        assert [p["ratio"] for p in res["points"]] == [1 << i for i in range(12)]
+        assert all(p["hash_ms"] > 0 and p["sorted_ms"] > 0 for p in res["points"])
+        ratio = res["sorted_ratio"]
+        assert ratio == 0xFFFFFFFF or ratio in [p["ratio"] for p in res["points"]]
+        L, R = gen.pairwise_uniform(seed=1)
+        join_and_check(c, L, R, "after autotune")
+        with pytest.raises(MapsqError):
+            c.autotune(sorted_rows=100)
