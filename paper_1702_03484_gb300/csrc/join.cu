@@ -52,6 +52,7 @@ constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one 
 constexpr int kHllBits = 12;
 constexpr int kHllRegs = 1 << kHllBits;
 constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides size the table by rows
+constexpr int kHllSpan = 16;                           // row tiles per sketch CTA (one flush per 32K rows)
 constexpr int kBucket = 4;
 constexpr int kPhases = 9;
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA
@@ -225,16 +226,17 @@ __global__ void __launch_bounds__(kThreads) hll_kernel(const JoinDesc* __restric
   __shared__ uint32_t s[kHllRegs];
   const uint32_t j = item_join(first, k, blockIdx.x);
   const JoinDesc& d = jd[j];
-  const uint64_t base = (blockIdx.x - first[j]) * kRowTile;
+  const uint64_t base = (blockIdx.x - first[j]) * uint64_t(kRowTile) * kHllSpan;
   for (int r = threadIdx.x; r < kHllRegs; r += kThreads) s[r] = 0;
   __syncthreads();
-#pragma unroll
-  for (int it = 0; it < kRowItems; ++it) {
+#pragma unroll 4
+  for (int it = 0; it < kRowItems * kHllSpan; ++it) {
     const uint64_t i = base + uint64_t(it) * kThreads + threadIdx.x;
     if (i < d.nb) {
       const uint64_t h = mix_key(load_key(d.bk, i) ^ 0x9e3779b97f4a7c15ull);
       const uint64_t w = (h << kHllBits) | (1ull << (kHllBits - 1));
-      atomicMax(&s[h >> (64 - kHllBits)], uint32_t(__clzll(w) + 1));
+      const uint32_t reg = uint32_t(h >> (64 - kHllBits)), rho = uint32_t(__clzll(w) + 1);
+      if (s[reg] < rho) atomicMax(&s[reg], rho);  // most rows cannot raise their register
     }
   }
   __syncthreads();
@@ -400,6 +402,16 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (s[q] != kNoSlot) pos[q] += group_begin(d.t, s[q], group_of(d.t, s[q])->y);
+    if (nbv == 2) {
+      // a row's two values in one 8-byte store
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t i = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+        if (s[q] != kNoSlot)
+          reinterpret_cast<uint2*>(d.grouped)[pos[q]] = make_uint2(__ldcs(d.bsrc[0] + i), __ldcs(d.bsrc[1] + i));
+      }
+      continue;
+    }
     for (int c = 0; c < nbv; ++c) {
       uint32_t x[4];
 #pragma unroll
@@ -652,6 +664,22 @@ __device__ __forceinline__ void write_column(const uint32_t* __restrict__ src, c
   store_runs<kFull>(dst, x, n);
 }
 
+// A probe-side column when every run of the warp comes from one probe row
+// (runs of consecutive output rows of one row, the common case when rows have
+// several matches): one gather per run instead of one per row.
+template <bool kFull>
+__device__ __forceinline__ void write_column_runs(const uint32_t* __restrict__ src, const uint32_t (&idx)[kWriteRows],
+                                                  uint32_t* __restrict__ dst, uint32_t n) {
+  uint32_t x[kWriteRows];
+#pragma unroll
+  for (int g = 0; g < kRuns; ++g) {
+    const uint32_t v = kFull || run_row(g * kVec) < n ? __ldg(src + idx[g * kVec]) : 0u;
+#pragma unroll
+    for (int w = 0; w < kVec; ++w) x[g * kVec + w] = v;
+  }
+  store_runs<kFull>(dst, x, n);
+}
+
 // Two build-side columns stored together (row-major pairs): one 8-byte gather
 // per row feeds both; half of the thread's runs at a time.
 template <bool kFull>
@@ -765,9 +793,16 @@ __global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc*
 #pragma unroll
       for (int i = 0; i < kWriteRows; ++i) {
         const uint32_t q = run_row(i);
-        idx[i] = q < n ? s_map[mi(q)] : 0u;
+        idx[i] = s_map[mi(q < n ? q : n - 1)];  // rows past the tile's end repeat its last row (never stored)
       }
       const uint32_t st = side ? d.bstride : 1u;
+      bool runs_uniform = false;
+      if (!side) {
+        bool u = true;
+#pragma unroll
+        for (int g = 0; g < kRuns; ++g) u &= idx[g * kVec] == idx[g * kVec + kVec - 1];
+        runs_uniform = __all_sync(0xffffffffu, u);
+      }
       if (side && d.grouped && d.nbv == 2) {
         // both build columns from one 8-byte gather per row
         int c0 = -1, c1 = -1;
@@ -780,8 +815,14 @@ __global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc*
       for (int c = 0; c < d.ncols; ++c) {
         if (int((d.from_build >> c) & 1u) != side) continue;
         const uint32_t* src = side ? d.src[c] : d.src[c] + ilo;
-        if (n == kWriteTile) write_column<true>(src, idx, st, d.out[c] + t0, n);
-        else write_column<false>(src, idx, st, d.out[c] + t0, n);
+        if (runs_uniform) {
+          if (n == kWriteTile) write_column_runs<true>(src, idx, d.out[c] + t0, n);
+          else write_column_runs<false>(src, idx, d.out[c] + t0, n);
+        } else if (n == kWriteTile) {
+          write_column<true>(src, idx, st, d.out[c] + t0, n);
+        } else {
+          write_column<false>(src, idx, st, d.out[c] + t0, n);
+        }
       }
     }
     __syncthreads();
@@ -995,7 +1036,7 @@ struct BatchJoin {
       const JoinPlan& pl = plans[j];
       plans[j].M = pl.hash ? std::max<uint64_t>(1024, 2 * pl.nb) : 0;
       if (pl.hll) {
-        per[j] = ceil_div(pl.nb, kRowTile);
+        per[j] = ceil_div(pl.nb, uint64_t(kRowTile) * kHllSpan);
         ++nh;
       }
     }
@@ -1031,19 +1072,25 @@ struct BatchJoin {
     return MAPSQ_OK;
   }
 
-  // Descriptors and item offsets go up together, in one copy.
+  // Descriptors, item offsets and a zeroed tail go up together, in one copy.
+  // The tail holds the status word, the write phase's work counter and the
+  // joins' row counts, so that each upload resets the first two and one copy
+  // reads back all of them.
+  uint64_t* d_tail = nullptr;
   int upload_descs() {
-    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size();
+    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size(), tb = sizeof(uint64_t) * (2 + k);
     if (!d_descs) {
       unsigned char* blob = nullptr;
-      MQ_TRY(mem->get(db + fb, &blob));
+      MQ_TRY(mem->get(db + fb + tb, &blob));
       d_descs = reinterpret_cast<JoinDesc*>(blob);
       d_first = reinterpret_cast<uint64_t*>(blob + db);
+      d_tail = reinterpret_cast<uint64_t*>(blob + db + fb);
+      status = reinterpret_cast<uint32_t*>(d_tail);
     }
-    blob_host.resize(db + fb);
+    blob_host.assign(db + fb + tb, 0);
     memcpy(blob_host.data(), descs.data(), db);
     memcpy(blob_host.data() + db, first.data(), fb);
-    return upload(d_descs, blob_host.data(), db + fb);
+    return upload(d_descs, blob_host.data(), db + fb + tb);
   }
   std::vector<unsigned char> blob_host;
 
@@ -1105,7 +1152,7 @@ struct BatchJoin {
     return MAPSQ_OK;
   }
 
-  int count_phases(uint64_t* totals) {
+  int count_phases() {
     MQ_TRY(upload_descs());
     double bytes = 0;
     if (items(PH_INSERT)) {
@@ -1152,33 +1199,32 @@ struct BatchJoin {
       launched();
       done(r, bytes);
     }
-    tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 1, totals);
+    tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 1, d_tail + 2);
     launched();
     return cuda(cudaGetLastError(), "count phases");
   }
 
   int count() {
-    MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
     MQ_TRY(size_tables());
-    uint64_t* totals = nullptr;
-    MQ_TRY(mem->get(k, &totals));
     for (int attempt = 0;; ++attempt) {
       MQ_TRY(allocate());
-      MQ_TRY(count_phases(totals));
-      MQ_TRY(readback(totals, k));
-      const uint32_t st = uint32_t(host[k]);
+      MQ_TRY(count_phases());  // its upload zeroes the status word
+      // one copy: status word, work counter, row counts
+      host.assign(2 + k, 0);
+      MQ_TRY(cuda(cudaMemcpyAsync(host.data(), d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
+      MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
+      const uint32_t st = uint32_t(host[0]);
       if (st & 1u) {
         // a distinct-key estimate far too low: rebuild every table at two slots per build row
         if (attempt > 0) return fail(MAPSQ_ERR_CUDA, "hash table full");
         for (auto& pl : plans)
           if (pl.hash) pl.M = (std::max<uint64_t>(1024, 2 * pl.nb) + kBucket - 1) / kBucket * kBucket;
-        MQ_TRY(cuda(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream), "memset"));
         continue;
       }
       if (st & 4u)
         return fail(MAPSQ_ERR_UNSUPPORTED, "2048 consecutive probe rows with 2^32 or more matches");
       if (st) return fail(MAPSQ_ERR_CUDA, "device status word set");
-      for (uint32_t j = 0; j < k; ++j) plans[j].T = descs[j].T = host[j];
+      for (uint32_t j = 0; j < k; ++j) plans[j].T = descs[j].T = host[2 + j];
       return MAPSQ_OK;
     }
   }
@@ -1226,9 +1272,7 @@ struct BatchJoin {
     if (!items(PH_WRITE) && !items(PH_CROSS)) return MAPSQ_OK;
     MQ_TRY(upload_descs());
     if (items(PH_WRITE)) {
-      unsigned long long* queue = nullptr;
-      MQ_TRY(mem->get(1, &queue));
-      MQ_TRY(cuda(cudaMemsetAsync(queue, 0, 8, stream), "memset"));
+      unsigned long long* queue = reinterpret_cast<unsigned long long*>(d_tail + 1);  // zeroed by the upload
       int r = rec(K_PARTITION);
       write_partition_kernel<<<unsigned(items(PH_PART)), kThreads, 0, stream>>>(d_descs, phase_first(PH_PART), k);
       launched();
