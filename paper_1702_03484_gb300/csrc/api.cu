@@ -293,6 +293,8 @@ int mapsq_destroy(mapsq_ctx* ctx) {
   }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   while (!ctx->live_tables.empty()) table_release(ctx, ctx->live_tables.back());
+  for (void* p : ctx->chunk_cache) dev_free(ctx, p, Scratch::kChunk);
+  ctx->chunk_cache.clear();
   store_release(ctx);
   dev_free(ctx, ctx->d_status, 256);
   cudaStreamSynchronize(ctx->stream);
@@ -310,6 +312,8 @@ int mapsq_destroy(mapsq_ctx* ctx) {
 int mapsq_set_stream(mapsq_ctx* ctx, void* cuda_stream) {
   if (!ctx) return MAPSQ_ERR_INVALID;
   if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
+  // memory released to the context in the old stream's order (cached scratch) must be idle first
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->own_stream;
   return MAPSQ_OK;
 }

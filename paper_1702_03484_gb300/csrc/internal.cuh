@@ -122,6 +122,9 @@ struct mapsq_ctx {
   mapsq::KernelTotals totals[mapsq::K_COUNT_KERNELS];
   std::vector<mapsq::TableImpl*> live_tables;
   uint32_t sorted_ratio = 4;      // AUTO joins: sorted side rows / other side rows from which SORTED runs
+  // scratch chunks kept for the next call (reused in stream order on ``stream``)
+  static constexpr int kChunkCache = 4;
+  std::vector<void*> chunk_cache;
 };
 
 namespace mapsq {
@@ -158,7 +161,12 @@ struct Scratch {
   size_t left = 0;
   explicit Scratch(Ctx* c) : ctx(c) {}
   ~Scratch() {
-    for (auto& b : blocks) dev_free(ctx, b.first, b.second);
+    for (auto& b : blocks) {
+      if (b.second == kChunk && int(ctx->chunk_cache.size()) < Ctx::kChunkCache)
+        ctx->chunk_cache.push_back(b.first);  // work queued on the stream still reads it: reuse is stream-ordered
+      else
+        dev_free(ctx, b.first, b.second);
+    }
   }
   template <class T>
   int get(size_t count, T** out) {
@@ -167,7 +175,13 @@ struct Scratch {
     if (bytes > left) {
       void* p = nullptr;
       size_t chunk = bytes < kChunk ? kChunk : bytes;
-      int rc = dev_alloc(ctx, chunk, &p);
+      int rc = MAPSQ_OK;
+      if (chunk == kChunk && !ctx->chunk_cache.empty()) {
+        p = ctx->chunk_cache.back();
+        ctx->chunk_cache.pop_back();
+      } else {
+        rc = dev_alloc(ctx, chunk, &p);
+      }
       if (rc == MAPSQ_ERR_BUDGET && chunk > bytes) rc = dev_alloc(ctx, chunk = bytes, &p);  // just what fits
       if (rc != MAPSQ_OK) return rc;
       blocks.push_back({p, chunk});

@@ -1211,8 +1211,11 @@ struct BatchJoin {
       MQ_TRY(count_phases());  // its upload zeroes the status word
       // one copy: status word, work counter, row counts
       host.assign(2 + k, 0);
-      MQ_TRY(cuda(cudaMemcpyAsync(host.data(), d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
+      // through the context's pinned buffer when it is large enough (a pageable copy is slower)
+      uint64_t* dst = ctx && host.size() <= kPinnedWords ? ctx->h_pinned : host.data();
+      MQ_TRY(cuda(cudaMemcpyAsync(dst, d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
       MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
+      if (dst != host.data()) memcpy(host.data(), dst, host.size() * 8);
       const uint32_t st = uint32_t(host[0]);
       if (st & 1u) {
         // a distinct-key estimate far too low: rebuild every table at two slots per build row
