@@ -55,7 +55,7 @@ constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides si
 constexpr int kHllSpan = 16;                           // row tiles per sketch CTA (one flush per 32K rows)
 constexpr int kBucket = 4;
 constexpr int kPhases = 9;
-constexpr int kSamples = 2048;                         // sorted key column samples per count CTA
+constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
 constexpr int kSortedItems = kRowTile / kSortedThreads;
 constexpr uint32_t kSortedRatio = 4;                   // default: sorted side at least this many times the other's rows
@@ -543,7 +543,21 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
     if (row < np) {
       const uint32_t v = __ldcs(d.pk.c0 + row);
       const uint64_t lo = sorted_bound(x, nx, s_key, v, false);
-      const uint64_t hi = lo < nx && __ldg(x + lo) == v ? sorted_bound(x, nx, s_key, v, true) : lo;
+      uint64_t hi = lo;
+      if (lo < nx && __ldg(x + lo) == v) {
+        // end of the run: gallop from its start (short runs stay in one cache line), then bisect
+        uint64_t a = lo, step = 1;
+        while (a + step < nx && __ldg(x + a + step) == v) {
+          a += step;
+          step <<= 1;
+        }
+        uint64_t b = min(a + step, nx);  // x[a] == v; x[b] > v or b == nx
+        while (b - a > 1) {
+          const uint64_t m = a + (b - a) / 2;
+          if (__ldg(x + m) == v) a = m; else b = m;
+        }
+        hi = a + 1;
+      }
       cnt = uint32_t(hi - lo);
       __stcs(d.pbeg + row, cnt ? uint32_t(lo) : 0u);
     }
@@ -664,6 +678,30 @@ __device__ __forceinline__ void write_column(const uint32_t* __restrict__ src, c
   store_runs<kFull>(dst, x, n);
 }
 
+// A probe-side column in general: a run's first and last rows are gathered, a
+// middle row only when its probe row is neither of theirs (probe rows rise
+// along a run).
+template <bool kFull>
+__device__ __forceinline__ void write_column_ends(const uint32_t* __restrict__ src, const uint32_t (&idx)[kWriteRows],
+                                                  uint32_t* __restrict__ dst, uint32_t n) {
+  uint32_t x[kWriteRows];
+#pragma unroll
+  for (int g = 0; g < kRuns; ++g) {
+    const uint32_t a = idx[g * kVec], b = idx[g * kVec + kVec - 1];
+    const bool live = kFull || run_row(g * kVec) < n;
+    const uint32_t va = live ? __ldg(src + a) : 0u;
+    const uint32_t vb = live ? __ldg(src + b) : 0u;
+    x[g * kVec] = va;
+    x[g * kVec + kVec - 1] = vb;
+#pragma unroll
+    for (int w = 1; w < kVec - 1; ++w) {
+      const uint32_t i = idx[g * kVec + w];
+      x[g * kVec + w] = i == a ? va : i == b ? vb : (live ? __ldg(src + i) : 0u);
+    }
+  }
+  store_runs<kFull>(dst, x, n);
+}
+
 // A probe-side column when every run of the warp comes from one probe row
 // (runs of consecutive output rows of one row, the common case when rows have
 // several matches): one gather per run instead of one per row.
@@ -686,6 +724,22 @@ template <bool kFull>
 __device__ __forceinline__ void write_pair(const uint32_t* __restrict__ grouped, const uint32_t (&idx)[kWriteRows],
                                            uint32_t* __restrict__ dst0, uint32_t* __restrict__ dst1, uint32_t n) {
   constexpr int kHalf = kWriteRows / 2;
+  // every run of the warp reads four consecutive build rows starting at an even
+  // row: two 16-byte loads per run
+  bool u = true;
+#pragma unroll
+  for (int g = 0; g < kRuns; ++g) u &= idx[g * kVec + kVec - 1] == idx[g * kVec] + kVec - 1 && !(idx[g * kVec] & 1u);
+  if (__all_sync(0xffffffffu, u)) {
+#pragma unroll
+    for (int g = 0; g < kRuns; ++g) {
+      const uint32_t q = (uint32_t(g) * kThreads + threadIdx.x) * kVec;
+      const uint4* p = reinterpret_cast<const uint4*>(grouped + uint64_t(idx[g * kVec]) * 2);
+      const uint4 a = __ldg(p), b = __ldg(p + 1);
+      __stcs(reinterpret_cast<uint4*>(dst0 + q), make_uint4(a.x, a.z, b.x, b.z));
+      __stcs(reinterpret_cast<uint4*>(dst1 + q), make_uint4(a.y, a.w, b.y, b.w));
+    }
+    return;
+  }
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     uint2 v[kHalf];
@@ -818,6 +872,9 @@ __global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc*
         if (runs_uniform) {
           if (n == kWriteTile) write_column_runs<true>(src, idx, d.out[c] + t0, n);
           else write_column_runs<false>(src, idx, d.out[c] + t0, n);
+        } else if (!side) {
+          if (n == kWriteTile) write_column_ends<true>(src, idx, d.out[c] + t0, n);
+          else write_column_ends<false>(src, idx, d.out[c] + t0, n);
         } else if (n == kWriteTile) {
           write_column<true>(src, idx, st, d.out[c] + t0, n);
         } else {
