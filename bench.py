@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--workload", default="university_bgp",
                     choices=["university_bgp", "skewed_join", "pairwise_uniform", "uneven_batch", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sorted-ratio", type=int, default=0,
+                    help="fix the hash-vs-sorted crossover instead of autotuning it (profiler captures)")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: a reduced case of the workload for profiler captures (skewed_join: "
                          "2^24 x 2^22 rows over 2^20 key ids)")
@@ -428,6 +430,14 @@ def oracle_all_cores(args, budget_s=10.0):
     return rows / max(dt for _, _, dt in res), cores, units
 
 
+def tuned(ctx, args):
+    """The hash-vs-sorted crossover for this GPU: measured (not timed), or fixed."""
+    if args.sorted_ratio:
+        ctx.set_sorted_ratio(args.sorted_ratio)
+        return {"sorted_ratio": args.sorted_ratio, "points": [], "fixed": True}
+    return ctx.autotune()
+
+
 def make_workload(args):
     if args.size == "small":
         if args.workload != "skewed_join":
@@ -580,7 +590,7 @@ def run_ours(args):
 
     with Context(device=local) as ctx:
         w.setup_gpu(ctx)
-        tune = ctx.autotune()  # the hash-vs-sorted choice for this GPU (not timed)
+        tune = tuned(ctx, args)
         stream = torch.cuda.current_stream(dev)
         for _ in range(args.warmup - 1):
             w.run_gpu(ctx)
@@ -723,7 +733,7 @@ def run_serving(args):
     w = Serving()
     with Context(device=local) as ctx:
         w.setup_gpu(ctx)
-        tune = ctx.autotune()  # the hash-vs-sorted choice for this GPU (not timed)
+        tune = tuned(ctx, args)
         # warm-up stream, profiled in full: it names the kernel with the most device time
         ctx.reset_stats()
         ctx.set_profiling(True)

@@ -142,6 +142,11 @@ typedef struct {
  * (serving), OOM, BUDGET, CUDA. */
 MAPSQ_API int mapsq_autotune(mapsq_ctx* ctx, uint64_t sorted_rows, mapsq_autotune_result* out);
 
+/* Set the context's sorted ratio directly (what mapsq_autotune measures; the
+ * default is 4; 0xFFFFFFFF never takes the sorted join).  Errors: INVALID
+ * (ratio 0), BUSY (serving). */
+MAPSQ_API int mapsq_set_sorted_ratio(mapsq_ctx* ctx, uint32_t ratio);
+
 /* Serving loop options (mapsq_serve_start); zero fields choose defaults. */
 typedef struct {
   uint32_t max_active;        /* queries in flight at once (default 256) */

@@ -131,4 +131,13 @@ int mapsq_autotune(mapsq_ctx* ctx, uint64_t sorted_rows, mapsq_autotune_result* 
   return autotune(ctx, sorted_rows, out);
 }
 
+int mapsq_set_sorted_ratio(mapsq_ctx* ctx, uint32_t ratio) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
+  if (ratio == 0) return set_error(ctx, MAPSQ_ERR_INVALID, "sorted ratio 0");
+  ctx->sorted_ratio = ratio;
+  return MAPSQ_OK;
+}
+
 }  // extern "C"

@@ -107,6 +107,7 @@ _SIGNATURES = {
     "mapsq_launch_count": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
     "mapsq_join_noalloc": (C.c_int, [_TP, _TP, C.POINTER(_P), C.c_uint64, _TP, C.POINTER(C.c_uint64), _P]),
     "mapsq_autotune": (C.c_int, [_P, C.c_uint64, C.POINTER(AutotuneResult)]),
+    "mapsq_set_sorted_ratio": (C.c_int, [_P, C.c_uint32]),
     "mapsq_serve_start": (C.c_int, [_P, C.POINTER(ServeOpts)]),
     "mapsq_submit": (C.c_int, [_P, C.POINTER(Pattern), C.c_uint32, C.POINTER(C.c_uint64)]),
     "mapsq_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(_TP)]),
@@ -319,6 +320,10 @@ def mapsq_autotune(ctx, sorted_rows=0):
             "points": [{"ratio": r.ratio[i], "hash_ms": r.hash_ms[i], "sorted_ms": r.sorted_ms[i]} for i in range(n)]}
 
 
+def mapsq_set_sorted_ratio(ctx, ratio):
+    _check(ctx, lib().mapsq_set_sorted_ratio(ctx, ratio))
+
+
 def mapsq_serve_start(ctx, max_active=0, mem_budget_bytes=0):
     opts = ServeOpts(max_active=max_active, mem_budget_bytes=mem_budget_bytes)
     _check(ctx, lib().mapsq_serve_start(ctx, C.byref(opts)))
@@ -484,6 +489,9 @@ class Context:
 
     def autotune(self, sorted_rows=0):
         return mapsq_autotune(self.handle, sorted_rows)
+
+    def set_sorted_ratio(self, ratio):
+        mapsq_set_sorted_ratio(self.handle, ratio)
 
     def serve_start(self, max_active=0, mem_budget_bytes=0):
         mapsq_serve_start(self.handle, max_active, mem_budget_bytes)
