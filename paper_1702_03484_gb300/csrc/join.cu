@@ -48,6 +48,7 @@ constexpr int kWriteRows = 16;                         // output rows per thread
 constexpr int kWriteTile = kThreads * kWriteRows;      // output rows per write tile
 constexpr int kStageRows = 1800;                       // probe rows per stage chunk (48 KB of shared memory in all)
 constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
+constexpr int kEarlyTiles = 64;                        // joins of up to this many write tiles are partitioned by the count scan
 constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
 constexpr int kHllBits = 12;
 constexpr int kHllRegs = 1 << kHllBits;
@@ -337,6 +338,23 @@ __global__ void __launch_bounds__(kThreads) slot_scan_kernel(const JoinDesc* __r
   if (threadIdx.x == 0) d.slot_total[blockIdx.x - first[j]] = total;
 }
 
+template <class T>
+__device__ __forceinline__ uint64_t upper_bound_t(const T* a, uint64_t lo, uint64_t hi, uint64_t v) {
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (uint64_t(a[mid]) <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The probe row whose output range holds output row v (given the tile offsets).
+__device__ __forceinline__ uint64_t part_row(const JoinDesc& d, uint64_t v) {
+  const uint64_t nt = (d.np + kRowTile - 1) / kRowTile;
+  const uint64_t ct = upper_bound_t(d.tile_base, 0, nt + 1, v) - 1;
+  const uint64_t lo = ct * kRowTile, hi = min(lo + kRowTile, d.np);
+  return lo + upper_bound_t(d.local + lo, 0, hi - lo, v - d.tile_base[ct]) - 1;
+}
+
 // Exclusive scans of per-tile totals, one CTA per join: slot tile starts
 // (which = 0) or probe tile output offsets with the join's row count last
 // (which = 1).
@@ -379,6 +397,13 @@ __global__ void __launch_bounds__(1024) tiles_scan_kernel(JoinDesc* __restrict__
   if (threadIdx.x == 0) {
     out[n] = s_carry;
     if (which == 1) totals_out[blockIdx.x] = s_carry;
+  }
+  // a join of few write tiles gets its output partition here (saves a launch)
+  if (which == 1) {
+    __syncthreads();  // the tile offsets above are visible to the whole block
+    const uint64_t T = s_carry, ntiles = (T + kWriteTile - 1) / kWriteTile;
+    if (T && ntiles <= kEarlyTiles && threadIdx.x <= ntiles)
+      d.part[threadIdx.x] = part_row(d, min(uint64_t(threadIdx.x) * kWriteTile, T - 1));
   }
 }
 
@@ -426,13 +451,29 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
   }
 }
 
+// A join whose probe side is one tile needs no tile scan: the count kernel
+// writes its tile offsets, its row count and, for a small output, its write
+// partition (the whole block calls this after the tile's counts are stored).
+__device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t tile_sum, uint64_t* total) {
+  if (threadIdx.x == 0) {
+    d.tile_base[0] = 0;
+    d.tile_base[1] = tile_sum;
+    *total = tile_sum;
+  }
+  __syncthreads();  // offsets and the tile's local offsets visible to the block
+  const uint64_t ntw = (tile_sum + kWriteTile - 1) / kWriteTile;
+  if (tile_sum && ntw <= kEarlyTiles && threadIdx.x <= ntw)
+    d.part[threadIdx.x] = part_row(d, min(uint64_t(threadIdx.x) * kWriteTile, tile_sum - 1));
+}
+
 // Count phase, tile-local: every probe row's match count and group start (four
 // lookups in flight per thread), the exclusive prefix sums of the counts inside
 // its tile of kRowTile rows (``local``), and the tile's total.  No CTA waits
 // for another; the tile totals are scanned afterwards.
 __global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc* __restrict__ jd,
                                                                   const uint64_t* first, uint32_t k,
-                                                                  uint32_t* __restrict__ status) {
+                                                                  uint32_t* __restrict__ status,
+                                                                  uint64_t* __restrict__ totals) {
   __shared__ uint32_t s_cnt[kRowTile + kRowTile / 32];
   __shared__ uint64_t s_warp[kThreads / 32];
   const uint32_t jj = item_join(first, k, blockIdx.x);
@@ -495,35 +536,23 @@ __global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc
     d.tile_total[tile] = tile_sum;
     if (tile_sum > 0xffffffffull) atomicOr(status, 4u);  // tile-local offsets would not fit in 32 bits
   }
+  if (np <= kRowTile) single_tile_finish(d, tile_sum, totals + jj);
 }
 
 // Count phase of a sorted join.  The build side's key column is sorted, so a
-// key's group is the run of equal keys: every probe row finds its run by two
-// searches (first position >= key, first position > key), narrowed first in
-// kSamples evenly spaced samples of the column held in shared memory, then in
-// global memory between two neighbouring samples.  Counts, group starts and
-// tile-local offsets are then written as in the hash count phase.
+// key's group is the run of equal keys: every probe row finds the run's start
+// by a search narrowed first in kSamples evenly spaced samples of the column
+// held in shared memory, then by bisection in global memory between two
+// neighbouring samples, and the run's end by galloping from its start.
+// Counts, group starts and tile-local offsets are then written as in the hash
+// count phase.
 __device__ __forceinline__ uint64_t sample_pos(uint32_t i, uint64_t n) { return uint64_t(i) * n / kSamples; }
 
-__device__ __forceinline__ uint64_t sorted_bound(const uint32_t* __restrict__ x, uint64_t n,
-                                                 const uint32_t* s_key, uint32_t v, bool upper) {
-  uint32_t a = 0, b = kSamples;  // first sample past v
-  while (a < b) {
-    const uint32_t m = (a + b) >> 1;
-    if (upper ? s_key[m] <= v : s_key[m] < v) a = m + 1; else b = m;
-  }
-  uint64_t lo = a ? sample_pos(a - 1, n) + 1 : 0, hi = a < kSamples ? sample_pos(a, n) : n;
-  while (lo < hi) {
-    const uint64_t m = lo + (hi - lo) / 2;
-    const uint32_t xm = __ldg(x + m);
-    if (upper ? xm <= v : xm < v) lo = m + 1; else hi = m;
-  }
-  return lo;
-}
 
 __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const JoinDesc* __restrict__ jd,
                                                                      const uint64_t* first, uint32_t k,
-                                                                     uint32_t* __restrict__ status) {
+                                                                     uint32_t* __restrict__ status,
+                                                                     uint64_t* __restrict__ totals) {
   __shared__ uint32_t s_key[kSamples];
   __shared__ uint32_t s_cnt[kRowTile + kRowTile / 32];
   __shared__ uint64_t s_warp[kSortedThreads / 32];
@@ -535,18 +564,53 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
   auto pad = [](int i) { return i + (i >> 5); };
   for (int i = threadIdx.x; i < kSamples; i += kSortedThreads) s_key[i] = __ldg(x + sample_pos(uint32_t(i), nx));
   __syncthreads();
+  // first position >= key: bracket from the samples, then the thread's rows
+  // bisect their brackets in lockstep (their loads overlap)
+  uint32_t key[kSortedItems];
+  uint64_t lo[kSortedItems], len[kSortedItems];
+#pragma unroll
+  for (int it = 0; it < kSortedItems; ++it) {
+    const uint64_t row = base + it * kSortedThreads + threadIdx.x;
+    key[it] = row < np ? __ldcs(d.pk.c0 + row) : 0u;
+    uint32_t a = 0, b = kSamples;
+    while (a < b) {
+      const uint32_t m = (a + b) >> 1;
+      if (s_key[m] < key[it]) a = m + 1; else b = m;
+    }
+    lo[it] = a ? sample_pos(a - 1, nx) + 1 : 0;
+    len[it] = row < np ? (a < kSamples ? sample_pos(a, nx) : nx) - lo[it] : 0;
+  }
+  for (;;) {
+    bool more = false;
+#pragma unroll
+    for (int it = 0; it < kSortedItems; ++it) more |= len[it] != 0;
+    if (!more) break;
+    uint32_t xm[kSortedItems];
+#pragma unroll
+    for (int it = 0; it < kSortedItems; ++it) xm[it] = len[it] ? __ldg(x + lo[it] + len[it] / 2) : 0u;
+#pragma unroll
+    for (int it = 0; it < kSortedItems; ++it) {
+      if (!len[it]) continue;
+      const uint64_t h = len[it] / 2;
+      if (xm[it] < key[it]) {
+        lo[it] += h + 1;
+        len[it] -= h + 1;
+      } else {
+        len[it] = h;
+      }
+    }
+  }
 #pragma unroll
   for (int it = 0; it < kSortedItems; ++it) {
     const int loc = it * kSortedThreads + threadIdx.x;
     const uint64_t row = base + loc;
     uint32_t cnt = 0;
     if (row < np) {
-      const uint32_t v = __ldcs(d.pk.c0 + row);
-      const uint64_t lo = sorted_bound(x, nx, s_key, v, false);
-      uint64_t hi = lo;
-      if (lo < nx && __ldg(x + lo) == v) {
+      const uint32_t v = key[it];
+      const uint64_t first_pos = lo[it];
+      if (first_pos < nx && __ldg(x + first_pos) == v) {
         // end of the run: gallop from its start (short runs stay in one cache line), then bisect
-        uint64_t a = lo, step = 1;
+        uint64_t a = first_pos, step = 1;
         while (a + step < nx && __ldg(x + a + step) == v) {
           a += step;
           step <<= 1;
@@ -556,10 +620,9 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
           const uint64_t m = a + (b - a) / 2;
           if (__ldg(x + m) == v) a = m; else b = m;
         }
-        hi = a + 1;
+        cnt = uint32_t(a + 1 - first_pos);
       }
-      cnt = uint32_t(hi - lo);
-      __stcs(d.pbeg + row, cnt ? uint32_t(lo) : 0u);
+      __stcs(d.pbeg + row, cnt ? uint32_t(first_pos) : 0u);
     }
     s_cnt[pad(loc)] = cnt;
   }
@@ -589,6 +652,7 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
     d.tile_total[tile] = tile_sum;
     if (tile_sum > 0xffffffffull) atomicOr(status, 4u);  // tile-local offsets would not fit in 32 bits
   }
+  if (np <= kRowTile) single_tile_finish(d, tile_sum, totals + jj);
 }
 
 // Output offset of probe row i of a join (i == np gives its row count).
@@ -596,14 +660,6 @@ __device__ __forceinline__ uint64_t off_at(const JoinDesc& d, uint64_t i) {
   return i < d.np ? d.tile_base[i / kRowTile] + d.local[i] : d.T;
 }
 
-template <class T>
-__device__ __forceinline__ uint64_t upper_bound_t(const T* a, uint64_t lo, uint64_t hi, uint64_t v) {
-  while (lo < hi) {
-    const uint64_t mid = lo + (hi - lo) / 2;
-    if (uint64_t(a[mid]) <= v) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 // The probe row whose output range holds output row v, searched in [lo, hi).
 __device__ __forceinline__ uint64_t row_of(const JoinDesc& d, uint64_t v, uint64_t lo, uint64_t hi) {
@@ -613,6 +669,7 @@ __device__ __forceinline__ uint64_t row_of(const JoinDesc& d, uint64_t v, uint64
   }
   return lo - 1;
 }
+
 
 // Merge-path partition of each join's output: part[t] = the probe row whose
 // output range holds output row min(t * kWriteTile, T - 1), t in [0, ntiles]:
@@ -624,11 +681,7 @@ __global__ void __launch_bounds__(kThreads) write_partition_kernel(const JoinDes
   const uint64_t t = (blockIdx.x - first[j]) * kThreads + threadIdx.x;
   const uint64_t ntiles = (d.T + kWriteTile - 1) / kWriteTile;
   if (t > ntiles) return;
-  const uint64_t v = min(t * uint64_t(kWriteTile), d.T - 1);
-  const uint64_t nt = (d.np + kRowTile - 1) / kRowTile;
-  const uint64_t ct = upper_bound_t(d.tile_base, 0, nt + 1, v) - 1;
-  const uint64_t lo = ct * kRowTile, hi = min(lo + kRowTile, d.np);
-  d.part[t] = lo + upper_bound_t(d.local + lo, 0, hi - lo, v - d.tile_base[ct]) - 1;
+  d.part[t] = part_row(d, min(t * uint64_t(kWriteTile), d.T - 1));
 }
 
 __device__ __forceinline__ uint32_t upper_bound_u32(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t v) {
@@ -1172,6 +1225,7 @@ struct BatchJoin {
       JoinDesc& d = descs[j];
       if (pl.sorted) {
         const uint64_t nt = ceil_div(pl.np, kRowTile);
+        MQ_TRY(mem->get(kEarlyTiles + 1, &d.part));
         MQ_TRY(mem->get(pl.np, &d.local));
         MQ_TRY(mem->get(pl.np, &d.pbeg));
         MQ_TRY(mem->get(nt, &d.tile_total));
@@ -1192,6 +1246,7 @@ struct BatchJoin {
       MQ_TRY(mem->get(pl.nb, &d.slot_of));
       MQ_TRY(mem->get(pl.nb, &d.rank_of));
       if (d.nbv) MQ_TRY(mem->get(pl.nb * d.nbv, &d.grouped));
+      MQ_TRY(mem->get(kEarlyTiles + 1, &d.part));
       MQ_TRY(mem->get(pl.np, &d.local));
       MQ_TRY(mem->get(pl.np, &d.pbeg));
       MQ_TRY(mem->get(nt, &d.tile_total));
@@ -1243,7 +1298,7 @@ struct BatchJoin {
       for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.np : 0;
       const int r = rec(K_PROBE_COUNT);
       probe_count_kernel<<<unsigned(items(PH_COUNT)), kThreads, 0, stream>>>(d_descs, phase_first(PH_COUNT), k,
-                                                                             status);
+                                                                             status, d_tail + 2);
       launched();
       done(r, bytes);
     }
@@ -1252,12 +1307,17 @@ struct BatchJoin {
       for (auto& pl : plans) bytes += pl.sorted ? 4.0 * pl.np : 0;
       const int r = rec(K_SORTED_COUNT);
       sorted_count_kernel<<<unsigned(items(PH_SORTED)), kSortedThreads, 0, stream>>>(d_descs, phase_first(PH_SORTED),
-                                                                                     k, status);
+                                                                                     k, status, d_tail + 2);
       launched();
       done(r, bytes);
     }
-    tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 1, d_tail + 2);
-    launched();
+    // joins of more than one probe tile need the scan of their tile totals
+    bool scan = false;
+    for (auto& pl : plans) scan |= (pl.hash || pl.sorted) && pl.np > uint64_t(kRowTile);
+    if (scan) {
+      tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 1, d_tail + 2);
+      launched();
+    }
     return cuda(cudaGetLastError(), "count phases");
   }
 
@@ -1284,7 +1344,10 @@ struct BatchJoin {
       if (st & 4u)
         return fail(MAPSQ_ERR_UNSUPPORTED, "2048 consecutive probe rows with 2^32 or more matches");
       if (st) return fail(MAPSQ_ERR_CUDA, "device status word set");
-      for (uint32_t j = 0; j < k; ++j) plans[j].T = descs[j].T = host[2 + j];
+      for (uint32_t j = 0; j < k; ++j) {
+        const JoinPlan& pl = plans[j];
+        plans[j].T = descs[j].T = pl.cross ? pl.np * pl.nb : pl.hash || pl.sorted ? host[2 + j] : 0;
+      }
       return MAPSQ_OK;
     }
   }
@@ -1320,8 +1383,10 @@ struct BatchJoin {
         cr[j] = ntiles;
         cbytes += 4.0 * pl.T * pl.lay.ncols + in;
       } else {
-        MQ_TRY(mem->get(ntiles + 1, &d.part));
-        part[j] = ceil_div(ntiles + 1, kThreads);
+        if (ntiles > kEarlyTiles) {  // else the count scan wrote the partition
+          MQ_TRY(mem->get(ntiles + 1, &d.part));
+          part[j] = ceil_div(ntiles + 1, kThreads);
+        }
         wr[j] = ntiles;
         bytes += 4.0 * pl.T * pl.lay.ncols + in;
       }
@@ -1333,11 +1398,13 @@ struct BatchJoin {
     MQ_TRY(upload_descs());
     if (items(PH_WRITE)) {
       unsigned long long* queue = reinterpret_cast<unsigned long long*>(d_tail + 1);  // zeroed by the upload
-      int r = rec(K_PARTITION);
-      write_partition_kernel<<<unsigned(items(PH_PART)), kThreads, 0, stream>>>(d_descs, phase_first(PH_PART), k);
-      launched();
-      done(r, 8.0 * items(PH_WRITE));
-      r = rec(K_JOIN_WRITE);
+      if (items(PH_PART)) {
+        const int r = rec(K_PARTITION);
+        write_partition_kernel<<<unsigned(items(PH_PART)), kThreads, 0, stream>>>(d_descs, phase_first(PH_PART), k);
+        launched();
+        done(r, 8.0 * items(PH_WRITE));
+      }
+      int r = rec(K_JOIN_WRITE);
       const unsigned grid = unsigned(std::min<uint64_t>(items(PH_WRITE), 152ull * 4));
       join_write_kernel<<<grid, kThreads, 0, stream>>>(d_descs, phase_first(PH_WRITE), k, queue);
       launched();
