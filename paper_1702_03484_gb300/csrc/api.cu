@@ -174,9 +174,14 @@ static int drain_profile(Ctx* ctx) {
 
 int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return MAPSQ_OK;
+  // Slots are used in order; an event is recorded after the last slot of each
+  // half of the ring, and a slot is reused only after the event of its half
+  // (recorded after the slot's previous copy was queued) has completed.
   const int s = ctx->stage_next;
   ctx->stage_next = (s + 1) % Ctx::kStageSlots;
-  if (ctx->stage_done[s]) MQ_CUDA(cudaEventSynchronize(ctx->stage_done[s]));
+  constexpr int kHalf = Ctx::kStageSlots / 2;
+  const int mark = (s / kHalf) * kHalf + kHalf - 1;  // the slot whose event covers this half
+  if (ctx->stage_done[mark]) MQ_CUDA(cudaEventSynchronize(ctx->stage_done[mark]));
   if (bytes > ctx->h_stage_bytes[s]) {
     if (ctx->h_stage[s]) cudaFreeHost(ctx->h_stage[s]);
     ctx->h_stage[s] = nullptr;
@@ -187,8 +192,10 @@ int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes) {
   }
   memcpy(ctx->h_stage[s], src, bytes);
   MQ_CUDA(cudaMemcpyAsync(dst, ctx->h_stage[s], bytes, cudaMemcpyHostToDevice, ctx->stream));
-  if (!ctx->stage_done[s]) MQ_CUDA(cudaEventCreateWithFlags(&ctx->stage_done[s], cudaEventDisableTiming));
-  MQ_CUDA(cudaEventRecord(ctx->stage_done[s], ctx->stream));
+  if (s == mark) {
+    if (!ctx->stage_done[s]) MQ_CUDA(cudaEventCreateWithFlags(&ctx->stage_done[s], cudaEventDisableTiming));
+    MQ_CUDA(cudaEventRecord(ctx->stage_done[s], ctx->stream));
+  }
   return MAPSQ_OK;
 }
 

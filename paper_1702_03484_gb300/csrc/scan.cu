@@ -158,7 +158,7 @@ int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* ou
   uint64_t* dout = nullptr;
   MQ_TRY(scratch.get(n, &dq));
   MQ_TRY(scratch.get(2 * size_t(n), &dout));
-  MQ_CUDA(cudaMemcpyAsync(dq, q.data(), n * sizeof(RangeQuery), cudaMemcpyHostToDevice, ctx->stream));
+  MQ_TRY(stage_upload(ctx, dq, q.data(), n * sizeof(RangeQuery)));  // pinned, asynchronous
   StoreCols sc{st.so_s, st.so_o, st.os_o, st.os_s};
   int rec = prof_begin(ctx, K_SCAN_RANGES);
   scan_ranges_kernel<<<(n + 3) / 4, 128, 0, ctx->stream>>>(dq, n, sc, dout);
