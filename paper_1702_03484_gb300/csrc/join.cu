@@ -453,17 +453,26 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
 
 // A join whose probe side is one tile needs no tile scan: the count kernel
 // writes its tile offsets, its row count and, for a small output, its write
-// partition (the whole block calls this after the tile's counts are stored).
-__device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t tile_sum, uint64_t* total) {
+// partition, searching the tile's offsets where the block still holds them in
+// shared memory (s_off[pad(i)] = output offset of probe row i).  The whole
+// block calls this after the offsets are in place.
+__device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t tile_sum, uint64_t* total,
+                                                   const uint32_t* s_off) {
   if (threadIdx.x == 0) {
     d.tile_base[0] = 0;
     d.tile_base[1] = tile_sum;
     *total = tile_sum;
   }
-  __syncthreads();  // offsets and the tile's local offsets visible to the block
   const uint64_t ntw = (tile_sum + kWriteTile - 1) / kWriteTile;
-  if (tile_sum && ntw <= kEarlyTiles && threadIdx.x <= ntw)
-    d.part[threadIdx.x] = part_row(d, min(uint64_t(threadIdx.x) * kWriteTile, tile_sum - 1));
+  if (tile_sum && ntw <= kEarlyTiles && threadIdx.x <= ntw) {
+    const uint32_t v = uint32_t(min(uint64_t(threadIdx.x) * kWriteTile, tile_sum - 1));
+    uint32_t lo = 0, hi = uint32_t(d.np);  // last probe row whose offset is <= v
+    while (lo < hi) {
+      const uint32_t m = (lo + hi) >> 1;
+      if (s_off[m + (m >> 5)] <= v) lo = m + 1; else hi = m;
+    }
+    d.part[threadIdx.x] = lo - 1;
+  }
 }
 
 // Count phase, tile-local: every probe row's match count and group start (four
@@ -536,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc
     d.tile_total[tile] = tile_sum;
     if (tile_sum > 0xffffffffull) atomicOr(status, 4u);  // tile-local offsets would not fit in 32 bits
   }
-  if (np <= kRowTile) single_tile_finish(d, tile_sum, totals + jj);
+  if (np <= kRowTile) single_tile_finish(d, tile_sum, totals + jj, s_cnt);
 }
 
 // Count phase of a sorted join.  The build side's key column is sorted, so a
@@ -652,7 +661,7 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
     d.tile_total[tile] = tile_sum;
     if (tile_sum > 0xffffffffull) atomicOr(status, 4u);  // tile-local offsets would not fit in 32 bits
   }
-  if (np <= kRowTile) single_tile_finish(d, tile_sum, totals + jj);
+  if (np <= kRowTile) single_tile_finish(d, tile_sum, totals + jj, s_cnt);
 }
 
 // Output offset of probe row i of a join (i == np gives its row count).
