@@ -48,6 +48,8 @@ constexpr int kWriteRows = 16;                         // output rows per thread
 constexpr int kWriteTile = kThreads * kWriteRows;      // output rows per write tile
 constexpr int kStageRows = 1800;                       // probe rows per stage chunk (48 KB of shared memory in all)
 constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
+constexpr int kProbeIn = 2;                            // probe rows in flight per thread
+constexpr int kProbeBlocks = 6;                        // probe CTAs per SM (register budget)
 constexpr int kEarlyTiles = 64;                        // joins of up to this many write tiles are partitioned by the count scan
 constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
 constexpr int kHllBits = 12;
@@ -479,7 +481,7 @@ __device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t t
 // lookups in flight per thread), the exclusive prefix sums of the counts inside
 // its tile of kRowTile rows (``local``), and the tile's total.  No CTA waits
 // for another; the tile totals are scanned afterwards.
-__global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc* __restrict__ jd,
+__global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(const JoinDesc* __restrict__ jd,
                                                                   const uint64_t* first, uint32_t k,
                                                                   uint32_t* __restrict__ status,
                                                                   uint64_t* __restrict__ totals) {
@@ -493,25 +495,25 @@ __global__ void __launch_bounds__(kThreads, 4) probe_count_kernel(const JoinDesc
   const uint64_t np = d.np;
   auto pad = [](int i) { return i + (i >> 5); };
 #pragma unroll
-  for (int h0 = 0; h0 < kRowItems; h0 += 4) {
-    uint64_t key[4];
-    uint32_t b[4], s[4];
-    ulonglong2 k01[4], k23[4];
+  for (int h0 = 0; h0 < kRowItems; h0 += kProbeIn) {
+    uint64_t key[kProbeIn];
+    uint32_t b[kProbeIn], s[kProbeIn];
+    ulonglong2 k01[kProbeIn], k23[kProbeIn];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kProbeIn; ++q) {
       const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
       key[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < kProbeIn; ++q)
       if (key[q] != kEmptyKey) load_bucket(t, key[q], &b[q], &k01[q], &k23[q]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kProbeIn; ++q) {
       const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
       s[q] = row < np ? find_slot(t, key[q], b[q], k01[q], k23[q]) : kNoSlot;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kProbeIn; ++q) {
       const int loc = (h0 + q) * kThreads + threadIdx.x;
       const uint64_t row = base + loc;
       const uint2 g = s[q] != kNoSlot ? *group_of(t, s[q]) : make_uint2(0u, 0u);
