@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kThreads) hll_kernel(const JoinDesc* __restric
   const uint64_t base = (blockIdx.x - first[j]) * uint64_t(kRowTile) * kHllSpan;
   for (int r = threadIdx.x; r < kHllRegs; r += kThreads) s[r] = 0;
   __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
   for (int it = 0; it < kRowItems * kHllSpan; ++it) {
     const uint64_t i = base + uint64_t(it) * kThreads + threadIdx.x;
     if (i < d.nb) {
@@ -262,7 +262,7 @@ double hll_estimate(const uint32_t* regs) {
 
 // Insert every build row's key; slot_of[i] = its group's slot, rank_of[i] = its
 // rank inside the group, counted in the group table (warp-aggregated).
-__global__ void __launch_bounds__(kThreads) hash_insert_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+__global__ void __launch_bounds__(kThreads, 8) hash_insert_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                               uint32_t k, uint32_t* __restrict__ status) {
   const uint32_t j = item_join(first, k, blockIdx.x);
   const JoinDesc& d = jd[j];
