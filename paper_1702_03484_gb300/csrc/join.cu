@@ -47,6 +47,7 @@ constexpr int kRowItems = kRowTile / kThreads;         // rows per thread
 constexpr int kWriteRows = 16;                         // output rows per thread per write tile
 constexpr int kWriteTile = kThreads * kWriteRows;      // output rows per write tile
 constexpr int kStageRows = 1800;                       // probe rows per stage chunk (48 KB of shared memory in all)
+constexpr int kWriteBlocks = 4;                        // write CTAs per SM (register budget)
 constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
 constexpr int kProbeIn = 2;                            // probe rows in flight per thread
 constexpr int kProbeBlocks = 6;                        // probe CTAs per SM (register budget)
@@ -96,6 +97,7 @@ struct JoinDesc {
   int nbv;                        // their number (row-major stride of ``grouped``)
   uint32_t* grouped;              // nb * nbv: build values grouped by key
   uint32_t* local;                // np: output offset of each probe row inside its tile
+  uint32_t* nzmask;               // np / 32 + 1: bit i % 32 of word i / 32 set when probe row i has a match
   uint32_t* pbeg;                 // np: group start of each probe row
   uint64_t* tile_total;           // per probe tile: its output rows
   uint64_t* tile_base;            // per probe tile + 1: output offset of the tile (last = T)
@@ -519,6 +521,8 @@ __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(con
       const uint2 g = s[q] != kNoSlot ? *group_of(t, s[q]) : make_uint2(0u, 0u);
       if (row < np) __stcs(d.pbeg + row, g.x ? group_begin(t, s[q], g.y) : 0u);
       s_cnt[pad(loc)] = g.x;
+      const unsigned nz = __ballot_sync(0xffffffffu, g.x != 0);  // the warp's 32 consecutive rows
+      if ((threadIdx.x & 31) == 0 && row < np) d.nzmask[row >> 5] = nz;
     }
   }
   __syncthreads();
@@ -636,6 +640,8 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
       __stcs(d.pbeg + row, cnt ? uint32_t(first_pos) : 0u);
     }
     s_cnt[pad(loc)] = cnt;
+    const unsigned nz = __ballot_sync(0xffffffffu, cnt != 0);  // the warp's 32 consecutive rows
+    if ((threadIdx.x & 31) == 0 && row < np) d.nzmask[row >> 5] = nz;
   }
   __syncthreads();
   uint32_t v[kSortedItems];
@@ -671,6 +677,16 @@ __device__ __forceinline__ uint64_t off_at(const JoinDesc& d, uint64_t i) {
   return i < d.np ? d.tile_base[i / kRowTile] + d.local[i] : d.T;
 }
 
+
+// The first probe row after row i that has a match (one exists: the caller
+// holds an output row beyond row i's range), from the match bitmask.
+__device__ __forceinline__ uint64_t next_nonzero(const JoinDesc& d, uint64_t i) {
+  uint64_t w = (i + 1) >> 5;
+  const uint64_t last = d.np >> 5;
+  uint32_t m = d.nzmask[w] & (~0u << ((i + 1) & 31));
+  while (!m && w < last) m = d.nzmask[++w];
+  return (w << 5) + __ffs(m) - 1;
+}
 
 // The probe row whose output range holds output row v, searched in [lo, hi).
 __device__ __forceinline__ uint64_t row_of(const JoinDesc& d, uint64_t v, uint64_t lo, uint64_t hi) {
@@ -838,7 +854,7 @@ __device__ __forceinline__ void write_pair(const uint32_t* __restrict__ grouped,
 // 32-bit search and a short walk, into a padded row map; (3) every thread takes
 // 16 rows striped over the block (a row per lane), reads their map entries once
 // per side, and writes the columns with 16-byte streaming stores.
-__global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+__global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                                  uint32_t k, unsigned long long* __restrict__ queue) {
   __shared__ uint32_t s_rel[kStageRows + 1];
   __shared__ uint32_t s_beg[kStageRows];
@@ -874,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 4) join_write_kernel(const JoinDesc*
         const uint32_t q = q0 + j;
         if (q >= n) break;
         const uint64_t r = t0 + q;
-        if (off_at(d, i + 1) <= r) i = row_of(d, r, i + 1, ihi + 1);
+        if (off_at(d, i + 1) <= r) i = next_nonzero(d, i);  // ranges are contiguous: the next matching row
         s_pk[mi(q)] = uint32_t(i - ilo);
         s_bk[mi(q)] = d.pbeg[i] + uint32_t(r - off_at(d, i));
       }
@@ -1237,6 +1253,7 @@ struct BatchJoin {
       if (pl.sorted) {
         const uint64_t nt = ceil_div(pl.np, kRowTile);
         MQ_TRY(mem->get(kEarlyTiles + 1, &d.part));
+        MQ_TRY(mem->get(pl.np / 32 + 1, &d.nzmask));
         MQ_TRY(mem->get(pl.np, &d.local));
         MQ_TRY(mem->get(pl.np, &d.pbeg));
         MQ_TRY(mem->get(nt, &d.tile_total));
@@ -1258,6 +1275,7 @@ struct BatchJoin {
       MQ_TRY(mem->get(pl.nb, &d.rank_of));
       if (d.nbv) MQ_TRY(mem->get(pl.nb * d.nbv, &d.grouped));
       MQ_TRY(mem->get(kEarlyTiles + 1, &d.part));
+      MQ_TRY(mem->get(pl.np / 32 + 1, &d.nzmask));
       MQ_TRY(mem->get(pl.np, &d.local));
       MQ_TRY(mem->get(pl.np, &d.pbeg));
       MQ_TRY(mem->get(nt, &d.tile_total));
