@@ -56,7 +56,7 @@ def parse():
                     help="fix the hash-vs-sorted crossover instead of autotuning it (profiler captures)")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: a reduced case of the workload for profiler captures (skewed_join: "
-                         "2^24 x 2^22 rows over 2^20 key ids)")
+                         "2^24 x 2^22 rows over 2^20 key ids; uneven_batch: rows per side up to 2^20)")
     return ap.parse_args()
 
 
@@ -220,9 +220,9 @@ class UnevenBatch(Workload):
     another."""
     name = "uneven_batch"
 
-    def __init__(self, seed=4, n_joins=256):
-        self.joins = [(L, R) for L, R, _ in gen.uneven_batch(seed=seed, n_joins=n_joins)]
-        self.config = {"workload": "uneven_batch", "joins": n_joins, "rows_per_side": "2^U[8,22]",
+    def __init__(self, seed=4, n_joins=256, log_hi=22.0):
+        self.joins = [(L, R) for L, R, _ in gen.uneven_batch(seed=seed, n_joins=n_joins, log_hi=log_hi)]
+        self.config = {"workload": "uneven_batch", "joins": n_joins, "rows_per_side": f"2^U[8,{log_hi:g}]",
                        "columns": "2-4", "zipf_s": "0 / 0.8 / 1.2 per join", "seed": seed,
                        "form": "mapsq_join_batch (all joins in one batch)",
                        "l2": "inputs larger than L2, flushed between steps"}
@@ -440,9 +440,11 @@ def tuned(ctx, args):
 
 def make_workload(args):
     if args.size == "small":
-        if args.workload != "skewed_join":
-            raise SystemExit("--size small exists for skewed_join only")
-        return SkewedJoin(log_a=24, log_b=22, log_keys=20)
+        if args.workload == "skewed_join":
+            return SkewedJoin(log_a=24, log_b=22, log_keys=20)
+        if args.workload == "uneven_batch":
+            return UnevenBatch(log_hi=20.0)
+        raise SystemExit("--size small exists for skewed_join and uneven_batch only")
     return WORKLOADS[args.workload]()
 
 

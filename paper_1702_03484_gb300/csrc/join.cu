@@ -28,6 +28,7 @@
 // table's other columns, then the right table's.  No shared variable: the cross
 // product, one key group holding every row.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -46,13 +47,14 @@ constexpr int kRowTile = 2048;                         // rows per work item (bu
 constexpr int kRowItems = kRowTile / kThreads;         // rows per thread
 constexpr int kWriteRows = 16;                         // output rows per thread per write tile
 constexpr int kWriteTile = kThreads * kWriteRows;      // output rows per write tile
-constexpr int kStageRows = 1800;                       // probe rows per stage chunk (48 KB of shared memory in all)
+constexpr int kStageRows = 1800;                       // probe rows per stage chunk
 constexpr int kWriteBlocks = 4;                        // write CTAs per SM (register budget)
 constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
 constexpr int kProbeIn = 2;                            // probe rows in flight per thread
 constexpr int kProbeBlocks = 6;                        // probe CTAs per SM (register budget)
 constexpr int kEarlyTiles = 64;                        // joins of up to this many write tiles are partitioned by the count scan
 constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
+constexpr int kWriteSmem = int(sizeof(uint32_t)) * (2 * kStageRows + 1 + 2 * kMapWords);  // write kernel's dynamic shared memory
 constexpr int kHllBits = 12;
 constexpr int kHllRegs = 1 << kHllBits;
 constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides size the table by rows
@@ -856,20 +858,22 @@ __device__ __forceinline__ void write_pair(const uint32_t* __restrict__ grouped,
 // per side, and writes the columns with 16-byte streaming stores.
 __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                                  uint32_t k, unsigned long long* __restrict__ queue) {
-  __shared__ uint32_t s_rel[kStageRows + 1];
-  __shared__ uint32_t s_beg[kStageRows];
-  __shared__ uint32_t s_pk[kMapWords];  // probe row of each output row (relative to the tile's first)
-  __shared__ uint32_t s_bk[kMapWords];  // build row of each output row
+  // dynamic shared memory (kWriteSmem bytes): the stage and the row map
+  extern __shared__ __align__(16) uint32_t s_dyn[];
+  uint32_t* s_rel = s_dyn;                   // kStageRows + 1
+  uint32_t* s_beg = s_rel + kStageRows + 1;  // kStageRows
+  uint32_t* s_pk = s_beg + kStageRows;       // kMapWords: probe row of each output row (relative to the tile's first)
+  uint32_t* s_bk = s_pk + kMapWords;         // kMapWords: build row of each output row
   __shared__ uint32_t s_skip;
-  __shared__ unsigned long long s_item;
+  __shared__ unsigned long long s_item[2];   // this tile's item and the next one's
   // row q lives at q + q / 32: conflict-free both for the 16 consecutive rows a
   // thread maps and for the rows striped over the block that it gathers
   auto mi = [](uint32_t q) { return q + (q >> 5); };
   const uint64_t nitems = first[k];
-  while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1ull);
-    __syncthreads();
-    const uint64_t item = s_item;
+  if (threadIdx.x == 0) s_item[0] = atomicAdd(queue, 1ull);
+  __syncthreads();
+  for (int cur = 0;; cur ^= 1) {
+    const uint64_t item = s_item[cur];
     if (item >= nitems) break;
     const uint32_t jj = item_join(first, k, item);
     const JoinDesc& d = jd[jj];
@@ -920,6 +924,8 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
       __syncthreads();
     }
     if (!staged) __syncthreads();
+    // the next item, fetched while this tile's columns are written (read after the closing barrier)
+    if (threadIdx.x == 0) s_item[cur ^ 1] = atomicAdd(queue, 1ull);
     // probe-side columns, then build-side columns: one index array live at a time
     for (int side = 0; side < 2; ++side) {
       const uint32_t* s_map = side ? s_bk : s_pk;
@@ -1435,7 +1441,16 @@ struct BatchJoin {
       }
       int r = rec(K_JOIN_WRITE);
       const unsigned grid = unsigned(std::min<uint64_t>(items(PH_WRITE), 152ull * 4));
-      join_write_kernel<<<grid, kThreads, 0, stream>>>(d_descs, phase_first(PH_WRITE), k, queue);
+      static std::atomic<uint64_t> smem_set[4] = {};  // devices (bit per device) whose attribute is set
+      int dev = 0;
+      MQ_TRY(cuda(cudaGetDevice(&dev), "cudaGetDevice"));
+      const uint64_t bit = uint64_t(1) << (dev & 63);
+      if (dev >= 256 || !(smem_set[dev >> 6].load() & bit)) {
+        MQ_TRY(cuda(cudaFuncSetAttribute(join_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWriteSmem),
+                    "cudaFuncSetAttribute"));
+        if (dev < 256) smem_set[dev >> 6] |= bit;
+      }
+      join_write_kernel<<<grid, kThreads, kWriteSmem, stream>>>(d_descs, phase_first(PH_WRITE), k, queue);
       launched();
       done(r, bytes);
     }
