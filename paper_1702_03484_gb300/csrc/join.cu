@@ -9,20 +9,25 @@
 // keys: one insert pass gives each row its key group and its rank inside the
 // group (warp-aggregated atomics), a prefix sum over the groups' sizes gives
 // each group's start, and a scatter pass writes the build side's value columns
-// grouped by key, row-major.  Reduce: every row of the other table (the probe
-// side) looks its key up and counts its matches (the size of its LEFT x RIGHT
-// cross product); tile-local prefix sums and a scan of the tile totals give
-// every probe row its output range; a partition pass finds, for every output
-// tile, the probe rows that feed it; the write pass then emits every LEFT x
-// RIGHT pair exactly once, partitioned by output position so that skewed keys
-// are spread over all SMs.
+// grouped by key, row-major.  When one table is already sorted on its (single)
+// key column (a run of the triple store) and large against the other, it is
+// itself the grouping (Algorithm 1's Sort step done by the store's order): no
+// table is built and each row of the other side searches it for its key's run
+// (the sorted join; the crossover is measured by the autotuner).  Reduce:
+// every row of the other table (the probe side) looks its key up and counts
+// its matches (the size of its LEFT x RIGHT cross product); tile-local prefix
+// sums and a scan of the tile totals give every probe row its output range; a
+// partition step finds, for every output tile, the probe rows that feed it;
+// the write pass then emits every LEFT x RIGHT pair exactly once, partitioned
+// by output position so that skewed keys are spread over all SMs.
 //
 // Batching: every phase is one launch for all the joins of a batch.  Its work
 // items (a join and a tile of that join) are numbered across the batch; a CTA
 // finds its join by a binary search of the per-join item offsets.  The write
 // phase is a persistent kernel that takes items from a device work counter.
 // A batch synchronises once, to size its outputs (twice when large build sides
-// need a distinct-key estimate).  A single join is a batch of one.
+// need a distinct-key estimate).  A single join is a batch of one; a join whose
+// probe side is one tile gets its offsets and partition from its count kernel.
 //
 // Output layout (Table 1(c)): shared variables in ascending id, then the left
 // table's other columns, then the right table's.  No shared variable: the cross
@@ -34,7 +39,6 @@
 #include <mutex>
 
 #include "internal.cuh"
-#include "lookback.cuh"
 
 namespace mapsq {
 
@@ -481,10 +485,11 @@ __device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t t
   }
 }
 
-// Count phase, tile-local: every probe row's match count and group start (four
-// lookups in flight per thread), the exclusive prefix sums of the counts inside
-// its tile of kRowTile rows (``local``), and the tile's total.  No CTA waits
-// for another; the tile totals are scanned afterwards.
+// Count phase, tile-local: every probe row's match count and group start
+// (kProbeIn lookups in flight per thread), the match bitmask, the exclusive
+// prefix sums of the counts inside its tile of kRowTile rows (``local``), and
+// the tile's total.  No CTA waits for another; the tile totals are scanned
+// afterwards (or, for a one-tile probe side, finished here).
 __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(const JoinDesc* __restrict__ jd,
                                                                   const uint64_t* first, uint32_t k,
                                                                   uint32_t* __restrict__ status,
@@ -1099,11 +1104,10 @@ struct BatchJoin {
     MQ_TRY(cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream), "upload"));
     return cuda(cudaStreamSynchronize(stream), "upload");  // pageable source: wait before it goes away
   }
-  // Reads ``words`` 64-bit words, then the status word into host[words].
+  // Reads ``words`` 64-bit words into host[0, words) (synchronises the stream).
   int readback(const void* dptr, size_t words) {
-    host.assign(words + 1, 0);
+    host.assign(words, 0);
     MQ_TRY(cuda(cudaMemcpyAsync(host.data(), dptr, words * 8, cudaMemcpyDeviceToHost, stream), "readback"));
-    MQ_TRY(cuda(cudaMemcpyAsync(host.data() + words, status, 4, cudaMemcpyDeviceToHost, stream), "status"));
     return cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
   }
   uint64_t* phase_first(int ph) { return d_first + size_t(ph) * (k + 1); }
