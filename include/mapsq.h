@@ -217,7 +217,8 @@ MAPSQ_API int mapsq_store_info(mapsq_ctx* ctx, uint64_t* n_triples, uint32_t* n_
  * distinct variable, in the order s, o; a variable in both places keeps the
  * triples with s == o.  Both constants: a 0-column table of 0 or 1 rows.  The
  * result may be a read-only view of the store's sorted columns (no copy); it
- * stays valid after the store is replaced, until it is freed.
+ * stays valid after the store is replaced, until it is freed.  Its
+ * sorted_mask marks the column the store keeps sorted.
  * Synchronises.  Errors: INVALID (NULL, var id > 15), UNSUPPORTED (variable
  * predicate), OOM, BUDGET, CUDA; INVALID if no store is loaded. */
 MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_table** out);
@@ -227,8 +228,11 @@ MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_
  * LEFT/RIGHT), shuffle by key, and reduce each key to every LEFT x RIGHT pair).
  * Output columns: the shared variables in ascending id, then the left table's
  * other columns in order, then the right table's (Table 1(c)).  No shared
- * variable: the cross product.  Input columns must be on the device.
- * Synchronises once (to size the output).  Errors: INVALID, UNSUPPORTED (more
+ * variable: the cross product.  Input columns must be on the device.  The
+ * shuffle is a hash build or, for a side sorted on the key column, the sorted
+ * join (``opts``: NULL or MAPSQ_JOIN_AUTO lets the context choose, see
+ * MAPSQ_JOIN_SORTED); the result is the same.  Synchronises once (to size the
+ * output).  Errors: INVALID (also an unknown algorithm), UNSUPPORTED (more
  * than two shared variables), OOM, BUDGET, CUDA. */
 MAPSQ_API int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right, mapsq_table** out,
                const mapsq_join_opts* opts);
