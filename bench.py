@@ -473,6 +473,22 @@ def make_workload(args):
 
 # ---------------------------------------------------------------- helpers
 
+def combine_ranks(total_ms, rows, world, device):
+    """Whole-job figures of N independent replicas: the slowest rank's timed
+    milliseconds and the sum of every rank's rows (max / sum all-reduces over
+    the default process group; ``device`` holds the tensors: a GPU for NCCL,
+    the CPU for gloo)."""
+    if world == 1:
+        return total_ms, rows
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    r = torch.tensor([float(rows)], dtype=torch.float64, device=device)
+    dist.all_reduce(r)
+    return float(t.item()), float(r.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -686,15 +702,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e_dt = time.perf_counter() - t0
 
-    t_max = total_ms
-    rows_all = rows
+    t_max, rows_all = combine_ranks(total_ms, rows, world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        r = torch.tensor([rows], device=dev, dtype=torch.float64)
-        dist.all_reduce(r)
-        rows_all = float(r.item())
         dist.destroy_process_group()
     if rank != 0:
         return
@@ -789,13 +798,8 @@ def run_serving(args):
         e_steps = max(1, min(args.steps, 4))
         e_rows, e_wall, _, h2d, d2h, e_counters, _ = w.serve(ctx, e_steps, part=3, to_host=True)
 
-    t_max, rows_all = dev_ms, rows
+    t_max, rows_all = combine_ranks(dev_ms, rows, world, "cuda")
     if world > 1:
-        t = torch.tensor([dev_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        r = torch.tensor([rows], device="cuda", dtype=torch.float64)
-        dist.all_reduce(r)
-        t_max, rows_all = float(t.item()), float(r.item())
         dist.destroy_process_group()
     if rank != 0:
         return
