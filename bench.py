@@ -515,6 +515,9 @@ class ClockSampler:
                  "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.perf_counter()  # sampling is live before the timed region starts
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
         return self
@@ -533,8 +536,10 @@ class ClockSampler:
 
     def summary(self):
         sm, mx, reasons = [], [], set()
+        # the first sample was taken before the timed region: keep it only if it is the only one
+        lines = self.lines[1:] if len(self.lines) > 1 else self.lines
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
