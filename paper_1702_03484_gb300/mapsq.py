@@ -248,9 +248,18 @@ def mapsq_table_from_columns(ctx, vars_, cols, nrows=None):
     return out
 
 
-def mapsq_table_to_host(ctx, t):
+def mapsq_table_to_host(ctx, t, out=None):
+    """Copy the columns to host memory: new numpy arrays, or the caller's
+    ``out`` arrays (uint32, at least nrows long each; pinned memory copies
+    fastest), of which the first nrows entries are returned as views."""
     tab = t.contents
-    cols = [np.empty(tab.nrows, dtype=np.uint32) for _ in range(tab.ncols)]
+    if out is None:
+        cols = [np.empty(tab.nrows, dtype=np.uint32) for _ in range(tab.ncols)]
+    else:
+        if len(out) < tab.ncols or any(o.dtype != np.uint32 or o.shape[0] < tab.nrows or not o.flags.c_contiguous
+                                       for o in out[: tab.ncols]):
+            raise ValueError("out: one contiguous uint32 array of at least nrows entries per column")
+        cols = [o[: tab.nrows] for o in out[: tab.ncols]]
     arr = (_P * max(tab.ncols, 1))(*[c.ctypes.data for c in cols])
     _check(ctx, lib().mapsq_table_to_host(ctx, t, arr))
     return list(tab.var[: tab.ncols]), cols
@@ -398,9 +407,9 @@ class TableRef:
         t = self.ptr.contents
         return list(t.var[: t.ncols])
 
-    def to_host(self):
-        """(vars, [numpy uint32 column, ...])"""
-        return mapsq_table_to_host(self.ctx.handle, self.ptr)
+    def to_host(self, out=None):
+        """(vars, [numpy uint32 column, ...]); ``out``: caller's arrays to fill."""
+        return mapsq_table_to_host(self.ctx.handle, self.ptr, out)
 
     def device_columns(self):
         """Zero-copy torch views of the device columns (valid until free)."""

@@ -288,3 +288,19 @@ def test_autotune_sets_ratio_and_joins_stay_exact():
         join_and_check(c, L, R, "after autotune")
         with pytest.raises(MapsqError):
             c.autotune(sorted_rows=100)
+
+
+def test_to_host_into_caller_arrays(ctx):
+    """mapsq_table_to_host into caller-provided (pinned) arrays equals the copy into new arrays."""
+    import torch
+    L, R = gen.pairwise_uniform(seed=1)
+    out = ctx.join(device_table(ctx, L), device_table(ctx, R))
+    vars_a, cols_a = out.to_host()
+    bufs = [torch.empty(out.nrows + 100, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+            for _ in range(len(out.vars))]
+    vars_b, cols_b = out.to_host(bufs)
+    assert vars_a == vars_b
+    assert all(np.array_equal(a, b) for a, b in zip(cols_a, cols_b))
+    with pytest.raises(ValueError):
+        out.to_host([np.zeros(3, np.uint32)] * len(out.vars))
+    out.free()
