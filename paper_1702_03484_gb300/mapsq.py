@@ -227,10 +227,18 @@ def mapsq_query_batch(ctx, bgps):
     return [outs[q] for q in range(nq)]
 
 
+def pattern_array(bgp):
+    """A BGP as the C array of mapsq_pattern that mapsq_query takes (build it
+    once to query the same BGP repeatedly without converting it each time)."""
+    if isinstance(bgp, C.Array):
+        return bgp
+    return (Pattern * len(bgp))(*[_pattern(tp) for tp in bgp])
+
+
 def mapsq_query(ctx, bgp):
-    arr = (Pattern * len(bgp))(*[_pattern(tp) for tp in bgp])
+    arr = pattern_array(bgp)
     out = _TP()
-    _check(ctx, lib().mapsq_query(ctx, arr, len(bgp), C.byref(out)))
+    _check(ctx, lib().mapsq_query(ctx, arr, len(arr), C.byref(out)))
     return out
 
 
