@@ -1,9 +1,11 @@
 // BGP evaluation, the host side of the paper's CPU/GPU coprocessing split
 // (Section 2): the host orders each BGP's patterns and drives the device's
 // pattern scans and joins, one pattern at a time, joining the partial results
-// after each match.  Many BGPs are evaluated together: their range searches are
-// one launch, and at every level each query's next join goes into one batched
-// join (every phase one launch for all of them).
+// after each match.  Each scan result is a view of the store sorted on the
+// variable it will be joined on, so the join may search it instead of hashing.
+// Many BGPs are evaluated together: their range searches are one launch, and
+// at every level each query's next join goes into one batched join (every
+// phase one launch for all of them).
 #include <algorithm>
 #include <vector>
 
@@ -20,10 +22,10 @@ uint32_t pattern_var_set(const mapsq_pattern& tp) {
   return m;
 }
 
-// Permute the columns of a result so that its variables are in ascending id
-// (a pointer permutation: no data moves).
 }  // namespace
 
+// Permute the columns of a result so that its variables are in ascending id
+// (a pointer permutation: no data moves; the sorted-column bits follow).
 void canonical_columns(mapsq_table* t) {
   const uint32_t n = t->ncols;
   for (uint32_t i = 1; i < n; ++i)
@@ -35,6 +37,9 @@ void canonical_columns(mapsq_table* t) {
     }
 }
 
+// The one variable that table t shares with pattern tp, or -1 (none, or two):
+// the variable a scan result will be joined on, so that it can be returned
+// sorted by it.
 int32_t shared_var(const mapsq_table& t, const mapsq_pattern& tp) {
   int32_t found = -1;
   int n = 0;

@@ -8,9 +8,12 @@
 // (every phase one launch for all of them), so that the steps of many queries
 // share launches and new arrivals join at any round.  Memory admission uses the
 // count pass: after the batch's counts, result tables are written in arrival
-// order while they fit in the budget; the rest wait for a later round.  A
-// finished query's result waits for mapsq_poll; the time from submission to
-// completion is recorded for the latency statistics.
+// order while they fit in the budget; the rest wait for a later round.  When
+// no join fits at all, the youngest query in flight is put back in the queue
+// (its tables freed) and admissions pause until a join is written, so the
+// oldest queries always progress.  A finished query's result waits for
+// mapsq_poll; the time from submission to completion (its kernels done) is
+// recorded for the latency statistics.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
