@@ -12,7 +12,7 @@ const char* const kKernelNames[K_COUNT_KERNELS] = {
     "store_radix_histogram", "store_radix_scatter", "store_dedup", "store_predicate_heads",
     "scan_ranges",           "scan_emit",           "scan_filter", "prefix_sum",
     "hash_insert",           "hash_scatter",        "probe_count", "join_write",
-    "cross_write",           "copy",        "hll_sketch",  "write_partition", "sorted_count"};
+    "cross_write",           "copy",        "hll_sketch",  "write_partition", "sorted_count", "dense_write"};
 
 int set_error(Ctx* ctx, int code, const char* fmt, ...) {
   if (ctx) {

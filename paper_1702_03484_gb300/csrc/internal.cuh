@@ -35,6 +35,7 @@ enum KernelId {
   K_HLL,
   K_PARTITION,
   K_SORTED_COUNT,
+  K_DENSE_WRITE,
   K_COUNT_KERNELS
 };
 

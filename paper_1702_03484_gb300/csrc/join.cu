@@ -64,13 +64,14 @@ constexpr int kHllRegs = 1 << kHllBits;
 constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides size the table by rows
 constexpr int kHllSpan = 16;                           // row tiles per sketch CTA (one flush per 32K rows)
 constexpr int kBucket = 4;
-constexpr int kPhases = 9;
+constexpr int kPhases = 10;
+constexpr uint32_t kDenseMax = 4;                      // joins of at most this many matches per probe row: dense write
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
 constexpr int kSortedItems = kRowTile / kSortedThreads;
 constexpr uint32_t kSortedRatio = 4;                   // default: sorted side at least this many times the other's rows
 
-enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS, PH_SORTED };
+enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS, PH_SORTED, PH_DENSE };
 
 // Open-addressing table of the build side's distinct keys: ``keys`` holds M
 // 64-bit keys in buckets of 4 (one 32-byte sector), probed bucket after bucket
@@ -461,6 +462,16 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
   }
 }
 
+// The join's largest match count of a probe row (atomic maximum over warps).
+template <int N>
+__device__ __forceinline__ void join_max_count(const uint32_t (&v)[N], uint64_t* out) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int q = 0; q < N; ++q) m = max(m, v[q]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)m);
+}
+
 // A join whose probe side is one tile needs no tile scan: the count kernel
 // writes its tile offsets, its row count and, for a small output, its write
 // partition, searching the tile's offsets where the block still holds them in
@@ -542,6 +553,7 @@ __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(con
   }
   uint64_t tile_sum;
   uint64_t run = block_scan(sum, s_warp, &tile_sum);
+  join_max_count(v, totals + k + jj);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < kRowItems; ++q) {
@@ -660,6 +672,7 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
   }
   uint64_t tile_sum;
   uint64_t run = block_scan_n<kSortedThreads>(sum, s_warp, &tile_sum);
+  join_max_count(v, totals + k + jj);
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < kSortedItems; ++q) {
@@ -977,6 +990,54 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
   }
 }
 
+// Write phase of a join whose probe rows have at most kDenseMax matches each:
+// a thread per probe row writes that row's output rows.  Consecutive threads
+// own consecutive probe rows, hence consecutive output ranges, so a warp's
+// stores of a column stay within a few lines; a row of exactly four matches
+// that starts at a multiple of four output rows takes one 16-byte store per
+// column.  No partition, no shared memory, no barrier.
+__global__ void __launch_bounds__(kThreads) dense_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+                                                              uint32_t k) {
+  const uint32_t jj = item_join(first, k, blockIdx.x);
+  const JoinDesc& d = jd[jj];
+  const uint64_t tile = blockIdx.x - first[jj];
+  const uint64_t base = tile * kRowTile, np = d.np;
+  const uint64_t tb = d.tile_base[tile];
+  const int ncols = d.ncols;
+  const uint32_t bstride = d.bstride;
+#pragma unroll 2
+  for (int it = 0; it < kRowItems; ++it) {
+    const uint64_t i = base + uint64_t(it) * kThreads + threadIdx.x;
+    if (i >= np) break;  // later rows of this thread are past the end too
+    const uint64_t o = tb + d.local[i];
+    const uint64_t e = i + 1 == np ? d.T : ((i + 1) % kRowTile ? tb + d.local[i + 1] : d.tile_base[tile + 1]);
+    const uint32_t c = uint32_t(e - o);
+    if (!c) continue;
+    const uint32_t g = d.pbeg[i];
+    const bool vec = c == kVec && !(o & (kVec - 1));
+    for (int col = 0; col < ncols; ++col) {
+      uint32_t* __restrict__ dst = d.out[col] + o;
+      const uint32_t* __restrict__ src = d.src[col];
+      uint32_t x[kVec];
+      if ((d.from_build >> col) & 1u) {
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) x[j] = uint32_t(j) < c ? __ldg(src + uint64_t(g + j) * bstride) : 0u;
+      } else {
+        const uint32_t v = __ldg(src + i);
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) x[j] = v;
+      }
+      if (vec) {
+        __stcs(reinterpret_cast<uint4*>(dst), make_uint4(x[0], x[1], x[2], x[3]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < kVec; ++j)
+          if (uint32_t(j) < c) __stcs(dst + j, x[j]);
+      }
+    }
+  }
+}
+
 // Cross products (no shared variable): output row r pairs probe row r / nb
 // with build row r % nb; items are output tiles of kWriteTile rows.
 __global__ void __launch_bounds__(kThreads) cross_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
@@ -1064,6 +1125,7 @@ struct JoinPlan {
   const int *bkey = nullptr, *pkey = nullptr;
   uint64_t nb = 0, np = 0, T = 0, M = 0;
   bool cross = false, hash = false, hll = false, sorted = false;
+  uint64_t maxc = 0;  // largest match count of a probe row (after the count phase)
 };
 
 // A batch of k joins, split in two halves so that the caller can allocate the
@@ -1220,12 +1282,12 @@ struct BatchJoin {
   }
 
   // Descriptors, item offsets and a zeroed tail go up together, in one copy.
-  // The tail holds the status word, the write phase's work counter and the
-  // joins' row counts, so that each upload resets the first two and one copy
-  // reads back all of them.
+  // The tail holds the status word, the write phase's work counter, the joins'
+  // row counts and their largest match counts per probe row, so that each
+  // upload resets the first two and one copy reads back all of them.
   uint64_t* d_tail = nullptr;
   int upload_descs() {
-    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size(), tb = sizeof(uint64_t) * (2 + k);
+    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size(), tb = sizeof(uint64_t) * (2 + 2 * k);
     if (!d_descs) {
       unsigned char* blob = nullptr;
       MQ_TRY(mem->get(db + fb + tb, &blob));
@@ -1366,7 +1428,7 @@ struct BatchJoin {
       MQ_TRY(allocate());
       MQ_TRY(count_phases());  // its upload zeroes the status word
       // one copy: status word, work counter, row counts
-      host.assign(2 + k, 0);
+      host.assign(2 + 2 * size_t(k), 0);
       // through the context's pinned buffer when it is large enough (a pageable copy is slower)
       uint64_t* dst = ctx && host.size() <= kPinnedWords ? ctx->h_pinned : host.data();
       MQ_TRY(cuda(cudaMemcpyAsync(dst, d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
@@ -1386,6 +1448,7 @@ struct BatchJoin {
       for (uint32_t j = 0; j < k; ++j) {
         const JoinPlan& pl = plans[j];
         plans[j].T = descs[j].T = pl.cross ? pl.np * pl.nb : pl.hash || pl.sorted ? host[2 + j] : 0;
+        plans[j].maxc = pl.hash || pl.sorted ? host[2 + k + j] : 0;
       }
       return MAPSQ_OK;
     }
@@ -1393,8 +1456,8 @@ struct BatchJoin {
 
   // Partition and write phases into out[j] (ncols device columns of T rows each).
   int write(uint32_t* const* const* out) {
-    std::vector<uint64_t> part(k, 0), wr(k, 0), cr(k, 0);
-    double bytes = 0, cbytes = 0;
+    std::vector<uint64_t> part(k, 0), wr(k, 0), cr(k, 0), dn(k, 0);
+    double bytes = 0, cbytes = 0, dbytes = 0;
     for (uint32_t j = 0; j < k; ++j) {
       const JoinPlan& pl = plans[j];
       JoinDesc& d = descs[j];
@@ -1421,6 +1484,9 @@ struct BatchJoin {
       if (pl.cross) {
         cr[j] = ntiles;
         cbytes += 4.0 * pl.T * pl.lay.ncols + in;
+      } else if (pl.maxc <= kDenseMax) {
+        dn[j] = ceil_div(pl.np, kRowTile);
+        dbytes += 4.0 * pl.T * pl.lay.ncols + in;
       } else {
         if (ntiles > kEarlyTiles) {  // else the count scan wrote the partition
           MQ_TRY(mem->get(ntiles + 1, &d.part));
@@ -1433,7 +1499,8 @@ struct BatchJoin {
     set_items(PH_PART, part);
     set_items(PH_WRITE, wr);
     set_items(PH_CROSS, cr);
-    if (!items(PH_WRITE) && !items(PH_CROSS)) return MAPSQ_OK;
+    set_items(PH_DENSE, dn);
+    if (!items(PH_WRITE) && !items(PH_CROSS) && !items(PH_DENSE)) return MAPSQ_OK;
     MQ_TRY(upload_descs());
     if (items(PH_WRITE)) {
       unsigned long long* queue = reinterpret_cast<unsigned long long*>(d_tail + 1);  // zeroed by the upload
@@ -1457,6 +1524,12 @@ struct BatchJoin {
       join_write_kernel<<<grid, kThreads, kWriteSmem, stream>>>(d_descs, phase_first(PH_WRITE), k, queue);
       launched();
       done(r, bytes);
+    }
+    if (items(PH_DENSE)) {
+      const int r = rec(K_DENSE_WRITE);
+      dense_write_kernel<<<unsigned(items(PH_DENSE)), kThreads, 0, stream>>>(d_descs, phase_first(PH_DENSE), k);
+      launched();
+      done(r, dbytes);
     }
     if (items(PH_CROSS)) {
       int r = rec(K_CROSS_WRITE);

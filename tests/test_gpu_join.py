@@ -185,9 +185,36 @@ def test_profiling_reports_kernels(ctx):
     join_and_check(ctx, L, R, "profiled")
     stats = ctx.kernel_stats()
     ctx.set_profiling(False)
-    for k in ("hash_insert", "hash_scatter", "probe_count", "prefix_sum", "join_write"):
+    write = "join_write" if "join_write" in stats else "dense_write"
+    for k in ("hash_insert", "hash_scatter", "probe_count", "prefix_sum", write):
         assert stats[k]["launches"] >= 1 and stats[k]["device_ms"] > 0
-    assert stats["join_write"]["alg_bytes"] > 12 * 30000
+    assert stats[write]["alg_bytes"] > 12 * 30000
+
+
+def test_dense_write_path(ctx):
+    """Joins of at most four matches per probe row take the dense write: rows of
+    exactly four aligned matches (16-byte stores) and of 0-3 matches (single
+    stores), hash and sorted sides, against the oracle."""
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    try:
+        r = gen.Rng(91)
+        # every build key exactly four times: probe rows match 0 or 4 rows
+        keys = np.repeat(np.unique(r.below(3000, 1 << 20).astype(np.uint32)), 4)
+        B = gen.Table([0, 12, 13], [keys, r.u32(keys.shape[0]), r.u32(keys.shape[0])])
+        A = gen.Table([0, 8], [np.concatenate((keys[::4][:2000], r.below(20000, 1 << 20).astype(np.uint32))),
+                               r.u32(22000)])
+        assert A.nrows > B.nrows  # B is the build side
+        join_and_check(ctx, A, B, "four matches")
+        # 1-3 copies per key: ragged runs
+        uk = np.unique(r.below(2000, 1 << 16).astype(np.uint32))
+        keys2 = np.concatenate([np.full(int(c), k, np.uint32) for k, c in zip(uk, r.between(uk.shape[0], 1, 3))])
+        B2 = gen.Table([0, 12], [keys2, r.u32(keys2.shape[0])])
+        A2 = gen.Table([0, 8, 9], [r.below(30000, 1 << 16).astype(np.uint32), r.u32(30000), r.u32(30000)])
+        join_and_check(ctx, A2, B2, "one to three matches")
+        assert ctx.kernel_stats()["dense_write"]["launches"] >= 2
+    finally:
+        ctx.set_profiling(False)
 
 
 def test_join_batch_matches_oracle(ctx):
