@@ -65,7 +65,8 @@ constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides si
 constexpr int kHllSpan = 16;                           // row tiles per sketch CTA (one flush per 32K rows)
 constexpr int kBucket = 4;
 constexpr int kPhases = 10;
-constexpr uint32_t kDenseMax = 4;                      // joins of at most this many matches per probe row: dense write
+constexpr int kDenseUnroll = 2;                        // probe rows of a thread unrolled in the dense write
+constexpr uint32_t kDenseMax = 16;                     // joins of at most this many matches per probe row: dense write
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
 constexpr int kSortedItems = kRowTile / kSortedThreads;
@@ -990,12 +991,13 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
   }
 }
 
-// Write phase of a join whose probe rows have at most kDenseMax matches each:
+// Write phase of a join whose probe rows have at most kDenseMax matches each
+// (16, the best of a sweep of 4, 8 and 16):
 // a thread per probe row writes that row's output rows.  Consecutive threads
 // own consecutive probe rows, hence consecutive output ranges, so a warp's
-// stores of a column stay within a few lines; a row of exactly four matches
-// that starts at a multiple of four output rows takes one 16-byte store per
-// column.  No partition, no shared memory, no barrier.
+// stores of a column stay within a few lines; every whole aligned run of four
+// output rows takes one 16-byte store per column.  No partition, no shared
+// memory, no barrier.
 __global__ void __launch_bounds__(kThreads) dense_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                               uint32_t k) {
   const uint32_t jj = item_join(first, k, blockIdx.x);
@@ -1005,7 +1007,7 @@ __global__ void __launch_bounds__(kThreads) dense_write_kernel(const JoinDesc* _
   const uint64_t tb = d.tile_base[tile];
   const int ncols = d.ncols;
   const uint32_t bstride = d.bstride;
-#pragma unroll 2
+#pragma unroll kDenseUnroll
   for (int it = 0; it < kRowItems; ++it) {
     const uint64_t i = base + uint64_t(it) * kThreads + threadIdx.x;
     if (i >= np) break;  // later rows of this thread are past the end too
@@ -1014,25 +1016,24 @@ __global__ void __launch_bounds__(kThreads) dense_write_kernel(const JoinDesc* _
     const uint32_t c = uint32_t(e - o);
     if (!c) continue;
     const uint32_t g = d.pbeg[i];
-    const bool vec = c == kVec && !(o & (kVec - 1));
     for (int col = 0; col < ncols; ++col) {
       uint32_t* __restrict__ dst = d.out[col] + o;
       const uint32_t* __restrict__ src = d.src[col];
-      uint32_t x[kVec];
-      if ((d.from_build >> col) & 1u) {
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) x[j] = uint32_t(j) < c ? __ldg(src + uint64_t(g + j) * bstride) : 0u;
-      } else {
-        const uint32_t v = __ldg(src + i);
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) x[j] = v;
-      }
-      if (vec) {
-        __stcs(reinterpret_cast<uint4*>(dst), make_uint4(x[0], x[1], x[2], x[3]));
-      } else {
+      const bool from_build = (d.from_build >> col) & 1u;
+      const uint32_t pv = from_build ? 0u : __ldg(src + i);
+      // chunks of four output rows: one 16-byte store when whole and aligned
+      for (uint32_t j0 = 0; j0 < c; j0 += kVec) {
+        uint32_t x[kVec];
 #pragma unroll
         for (int j = 0; j < kVec; ++j)
-          if (uint32_t(j) < c) __stcs(dst + j, x[j]);
+          x[j] = !from_build ? pv : j0 + j < c ? __ldg(src + uint64_t(g + j0 + j) * bstride) : 0u;
+        if (j0 + kVec <= c && !((o + j0) & (kVec - 1))) {
+          __stcs(reinterpret_cast<uint4*>(dst + j0), make_uint4(x[0], x[1], x[2], x[3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < kVec; ++j)
+            if (j0 + j < c) __stcs(dst + j0 + j, x[j]);
+        }
       }
     }
   }
