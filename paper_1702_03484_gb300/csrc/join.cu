@@ -65,7 +65,7 @@ constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides si
 constexpr int kHllSpan = 16;                           // row tiles per sketch CTA (one flush per 32K rows)
 constexpr int kBucket = 4;
 constexpr int kPhases = 10;
-constexpr int kDenseUnroll = 2;                        // probe rows of a thread unrolled in the dense write
+constexpr int kDenseUnroll = 4;                        // probe rows of a thread unrolled in the dense write
 constexpr uint32_t kDenseMax = 16;                     // joins of at most this many matches per probe row: dense write
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
