@@ -25,6 +25,11 @@
  * Results are multisets of rows (bag semantics, no DISTINCT); row order is
  * unspecified.
  *
+ * Citations.  Every call that computes a step of the method names the passage
+ * of the paper (Section, Algorithm or Table) that defines it.  The others
+ * (context and stream, errors, table memory, statistics, profiling) are
+ * infrastructure with no counterpart in the paper.
+ *
  * Conventions.  Every int-returning call returns MAPSQ_OK (0) or a negative
  * MAPSQ_ERR_* code; after an error, output arguments are left untouched and
  * ``mapsq_last_error`` describes it.  Input pointers are borrowed for the call
@@ -132,7 +137,8 @@ typedef struct {
   uint64_t sorted_rows;    /* rows of the sorted side in the test joins */
 } mapsq_autotune_result;
 
-/* Autotune the AUTO choice between the hash and the sorted join on this GPU:
+/* Autotune the AUTO choice between the hash and the sorted join on this GPU
+ * (two ways of Algorithm 1's Sort step; the choice is this library's):
  * joins a sorted side of ``sorted_rows`` rows (0 = 2^22; keys k / 2, so every
  * key twice) with other sides of sorted_rows / r rows (keys uniform over the
  * same range) for r = 1, 2, 4, ..., 2048, timing each algorithm (best of
@@ -237,7 +243,8 @@ MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_
 MAPSQ_API int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right, mapsq_table** out,
                const mapsq_join_opts* opts);
 
-/* Batched form: ``k`` independent joins (each as mapsq_join) evaluated
+/* Batched form: ``k`` independent joins (each as mapsq_join, Algorithm 1;
+ * evaluating many at once has no counterpart in the paper) evaluated
  * together.  Every phase of the join (hash build, count, partition, write) is
  * one launch for the whole batch, the write phase a persistent kernel fed by a
  * device work queue, and the batch synchronises once to size all outputs, so
@@ -253,7 +260,8 @@ MAPSQ_API int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* co
  * variables in ascending id.  Errors: as mapsq_scan_pattern and mapsq_join. */
 MAPSQ_API int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out);
 
-/* Batched form of mapsq_query: ``nq`` BGPs (bgps[q] with n[q] patterns)
+/* Batched form of mapsq_query: ``nq`` BGPs (bgps[q] with n[q] patterns, each
+ * evaluated as in Section 2; batching has no counterpart in the paper)
  * evaluated together.  Their range searches are one launch; at each level,
  * every query's next join goes into one batched join (mapsq_join_batch), so
  * the batch synchronises about once per level instead of once per join.
@@ -282,7 +290,8 @@ MAPSQ_API int mapsq_query_batch(mapsq_ctx* ctx, uint32_t nq, const mapsq_pattern
  * serving), INVALID (no store), OOM. */
 MAPSQ_API int mapsq_serve_start(mapsq_ctx* ctx, const mapsq_serve_opts* opts);
 
-/* Queue a BGP of ``n`` patterns (copied); *ticket identifies it.  Thread-safe.
+/* Queue a BGP of ``n`` patterns (copied; evaluated as in Section 2 by the
+ * serving loop); *ticket identifies it.  Thread-safe.
  * Errors: BUSY (not serving or stopping), INVALID, UNSUPPORTED. */
 MAPSQ_API int mapsq_submit(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, uint64_t* ticket);
 
