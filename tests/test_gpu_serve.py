@@ -171,3 +171,41 @@ def test_serving_state_errors(ctx, bgps):
     with pytest.raises(MapsqError) as e:
         ctx.serve_stop()
     assert e.value.name == "BUSY"
+
+
+def test_concurrent_submitters(ctx, bgps):
+    """Four threads submit at once (mapsq_submit is thread-safe) while the main
+    thread polls; every result equals the query alone."""
+    alone = _alone(ctx, bgps)
+    ctx.serve_start()
+    tickets = {}
+    lock = threading.Lock()
+
+    def submitter(offset):
+        for i in range(offset, len(bgps), 4):
+            t = ctx.submit(bgps[i])
+            with lock:
+                tickets[i] = t
+
+    threads = [threading.Thread(target=submitter, args=(o,)) for o in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    results = {}
+    deadline = time.time() + 120
+    while len(results) < len(bgps) and time.time() < deadline:
+        for i, t in tickets.items():
+            if i not in results:
+                r = ctx.poll(t)
+                if r is not None:
+                    results[i] = host_rows(r)
+                    r.free()
+        time.sleep(0.001)
+    stats = ctx.serve_stats()
+    ctx.serve_stop()
+    assert len(set(tickets.values())) == len(bgps)  # distinct tickets
+    assert len(results) == len(bgps)
+    for i, b in enumerate(bgps):
+        assert _same(results[i], alone[i]), b
+    assert stats["submitted"] == len(bgps) and stats["failed"] == 0
