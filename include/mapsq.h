@@ -374,8 +374,9 @@ MAPSQ_API int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches);
  * (its columns are ``out_cols``; the caller keeps ownership).
  *
  * Work runs on ``cuda_stream`` (a cudaStream_t of the current device).  The
- * call synchronises that stream once to read the row count; the output columns
- * are complete when the stream's later work is.  The first call on a device
+ * call synchronises that stream after each copy of its descriptors from host
+ * memory (it has no pinned buffer) and to read the row count; the output
+ * columns are complete when the stream's later work is.  The first call on a device
  * also looks up the array's device address, so make it before any stream
  * capture.  Every call shares the one array, and each call clears what must
  * start at zero, so calls whose device work overlaps (on two streams or two
