@@ -237,9 +237,11 @@ MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_
  * variable: the cross product.  Input columns must be on the device.  The
  * shuffle is a hash build or, for a side sorted on the key column, the sorted
  * join (``opts``: NULL or MAPSQ_JOIN_AUTO lets the context choose, see
- * MAPSQ_JOIN_SORTED); the result is the same.  Synchronises once (to size the
- * output).  Errors: INVALID (also an unknown algorithm), UNSUPPORTED (more
- * than two shared variables), OOM, BUDGET, CUDA. */
+ * MAPSQ_JOIN_SORTED); the result is the same.  Synchronises once to size the
+ * output (twice when a hash build side has 2^16 rows or more: its distinct
+ * keys are estimated first, to size the table).  Errors: INVALID (also an
+ * unknown algorithm), UNSUPPORTED (more than two shared variables), OOM,
+ * BUDGET, CUDA. */
 MAPSQ_API int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right, mapsq_table** out,
                const mapsq_join_opts* opts);
 
@@ -247,8 +249,9 @@ MAPSQ_API int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_ta
  * evaluating many at once has no counterpart in the paper) evaluated
  * together.  Every phase of the join (hash build, count, partition, write) is
  * one launch for the whole batch, the write phase a persistent kernel fed by a
- * device work queue, and the batch synchronises once to size all outputs, so
- * many small joins cost about as much as one.  out[j] receives join j's table.
+ * device work queue, and the batch synchronises once to size all outputs
+ * (twice with large hash build sides, as mapsq_join), so many small joins cost
+ * about as much as one.  out[j] receives join j's table.
  * Errors: as mapsq_join (then no table is returned). */
 MAPSQ_API int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* left,
                                const mapsq_table* const* right, mapsq_table** out, const mapsq_join_opts* opts);
