@@ -20,6 +20,9 @@ What it computes (MapSQ, arXiv 1702.03484):
   "partial matching"), a linear filter over the triple set.
 * ``evaluate_bgp``: pattern-at-a-time evaluation, joining the partial results
   after each pattern is matched (Section 2).
+* ``split_by_predicate``: the triple set grouped by predicate, so that a
+  pattern with a constant predicate is filtered against that predicate's
+  triples only (the same partial matches, a shorter linear filter).
 * ``brute_force_bgp``: every assignment of the variables over the graph's terms,
   kept when each substituted pattern is a triple of the graph (the SPARQL
   definition of a BGP's solutions).
@@ -175,6 +178,38 @@ def scan_pattern(graph, pattern):
     return vars_, np.stack([first_pos[v][mask] for v in vars_], axis=1).astype(np.uint32)
 
 
+def split_by_predicate(graph):
+    """The triple set cut into one triple set per predicate id: ``{p: (s, p, o)}``.
+
+    The same triples, grouped by their predicate, so that a pattern whose
+    predicate is a constant can be matched (still by a linear filter) against
+    the triples of that predicate only; the partial matches are unchanged."""
+    s, p, o = (np.asarray(x, dtype=np.uint32) for x in graph)
+    order = np.argsort(p, kind="stable")
+    ps = p[order]
+    cuts = np.flatnonzero(ps[1:] != ps[:-1]) + 1
+    starts = np.concatenate(([0], cuts)).astype(np.int64)
+    ends = np.concatenate((cuts, [ps.shape[0]])).astype(np.int64)
+    if ps.shape[0] == 0:
+        return {}
+    return {int(ps[a]): (s[order[a:b]], ps[a:b], o[order[a:b]]) for a, b in zip(starts, ends)}
+
+
+def _pattern_source(graph, pattern):
+    """The triples a pattern is matched against: the whole set, or, for a graph
+    split by predicate, the constant predicate's triples (all of them when the
+    predicate is a variable)."""
+    if not isinstance(graph, dict):
+        return graph
+    if pattern[3] & VAR_P:
+        parts = list(graph.values())
+        if not parts:
+            return tuple(np.zeros(0, np.uint32) for _ in range(3))
+        return tuple(np.concatenate([g[i] for g in parts]) for i in range(3))
+    empty = np.zeros(0, np.uint32)
+    return graph.get(int(pattern[1]), (empty, empty, empty))
+
+
 def pattern_vars(pattern):
     return {val for b, val in zip((VAR_S, VAR_P, VAR_O), pattern[:3]) if pattern[3] & b}
 
@@ -199,9 +234,13 @@ def evaluate_bgp(graph, bgp, order=None, join=join_mapreduce, is_set=False):
     """Pattern at a time: match each pattern, join the partial results in ``order``.
 
     ``is_set=True`` states that ``graph`` has no duplicate triples (for instance the
-    output of ``distinct_triples``), so the set step is skipped."""
-    g = graph if is_set else distinct_triples(*graph)
-    partial = [scan_pattern(g, pat) for pat in bgp]
+    output of ``distinct_triples``), so the set step is skipped.  ``graph`` may also
+    be the output of ``split_by_predicate`` applied to such a set."""
+    if isinstance(graph, dict):
+        g = graph
+    else:
+        g = graph if is_set else distinct_triples(*graph)
+    partial = [scan_pattern(_pattern_source(g, pat), pat) for pat in bgp]
     if order is None:
         order = smallest_first_order(bgp, [rows.shape[0] for _, rows in partial])
     acc = partial[order[0]]

@@ -243,6 +243,25 @@ def test_bgp_join_order_invariance_and_no_duplicates():
             assert multiset(oracle.evaluate_bgp(graph, bgp, order=order)) == ref
 
 
+def test_bgp_on_graph_split_by_predicate():
+    """Matching each pattern against its predicate's triples only (the graph
+    split by predicate) gives the same solutions as the whole triple set and as
+    brute force, variable predicates included."""
+    for seed in range(40):
+        graph = tiny_graph(seed + 300, n_terms=9, n_triples=28, n_pred=4)
+        g = oracle.distinct_triples(*graph)
+        split = oracle.split_by_predicate(g)
+        assert sum(v[0].shape[0] for v in split.values()) == g[0].shape[0]
+        assert all(np.all(v[1] == k) for k, v in split.items())
+        bgp = tiny_bgp(seed + 300, n_terms=9, n_pred=5)  # predicate 4 has no triples
+        if seed % 5 == 0:
+            s, p, o, m = bgp[0]
+            bgp[0] = (s, 3, o, m | 2)  # a variable predicate (id 3)
+        want = multiset(oracle.brute_force_bgp(graph, bgp))
+        assert multiset(oracle.evaluate_bgp(split, bgp)) == want, (seed, bgp)
+        assert multiset(oracle.evaluate_bgp(g, bgp, is_set=True)) == want
+
+
 def test_bgp_variable_repeated_in_pattern():
     s = np.array([1, 2, 3, 3], np.uint32)
     p = np.array([0, 0, 0, 1], np.uint32)
