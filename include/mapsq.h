@@ -367,8 +367,11 @@ MAPSQ_API int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches);
  *
  * ``left``/``right``: caller-described tables, columns on the current device,
  * 4-byte aligned.  The smaller input may have at most 262,144 rows and the
- * larger at most 1,048,576; larger inputs give MAPSQ_ERR_INVALID before any
- * device work.  ``out_cols``: one caller-owned device buffer per output column
+ * larger at most 1,048,576, whatever their order or sorted_mask (the join
+ * always groups the smaller input in a hash table); larger inputs give
+ * MAPSQ_ERR_INVALID before any device work.  A result of more than 2^32 rows
+ * gives MAPSQ_ERR_UNSUPPORTED (after the count, with ``*out_rows`` set).
+ * ``out_cols``: one caller-owned device buffer per output column
  * (shared variables, then the left table's other columns, then the right
  * table's), each 16-byte aligned with room for ``out_capacity_rows`` rows.  On
  * return ``*out_rows`` holds the join's row count; if it exceeds the capacity
@@ -385,7 +388,8 @@ MAPSQ_API int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches);
  * start at zero, so calls whose device work overlaps (on two streams or two
  * threads) race and must be serialised by the caller.  Errors: INVALID (NULL,
  * sizes beyond the limits, unaligned buffers), UNSUPPORTED (more than two
- * shared variables), BUDGET (output larger than the capacity), CUDA, TIMEOUT. */
+ * shared variables, more than 2^32 result rows), BUDGET (output larger than
+ * the capacity), CUDA, TIMEOUT. */
 MAPSQ_API int mapsq_join_noalloc(const mapsq_table* left, const mapsq_table* right, uint32_t* const* out_cols,
                                  uint64_t out_capacity_rows, mapsq_table* out, uint64_t* out_rows,
                                  void* cuda_stream);

@@ -169,6 +169,10 @@ struct Scratch {
         dev_free(ctx, b.first, b.second);
     }
   }
+  // Carved regions stay allocated until the destructor: a rewind is a no-op
+  // (the interface matches the fixed-array carver, which reuses its space).
+  size_t mark() const { return 0; }
+  void rewind(size_t) {}
   template <class T>
   int get(size_t count, T** out) {
     size_t bytes = count * sizeof(T);

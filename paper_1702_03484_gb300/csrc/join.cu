@@ -1287,16 +1287,21 @@ struct BatchJoin {
   // row counts and their largest match counts per probe row, so that each
   // upload resets the first two and one copy reads back all of them.
   uint64_t* d_tail = nullptr;
+  size_t blob_bytes() const { return sizeof(JoinDesc) * k + sizeof(uint64_t) * first.size() + sizeof(uint64_t) * (2 + 2 * k); }
+  int ensure_blob() {
+    if (d_descs) return MAPSQ_OK;
+    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size();
+    unsigned char* blob = nullptr;
+    MQ_TRY(mem->get(blob_bytes(), &blob));
+    d_descs = reinterpret_cast<JoinDesc*>(blob);
+    d_first = reinterpret_cast<uint64_t*>(blob + db);
+    d_tail = reinterpret_cast<uint64_t*>(blob + db + fb);
+    status = reinterpret_cast<uint32_t*>(d_tail);
+    return MAPSQ_OK;
+  }
   int upload_descs() {
     const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size(), tb = sizeof(uint64_t) * (2 + 2 * k);
-    if (!d_descs) {
-      unsigned char* blob = nullptr;
-      MQ_TRY(mem->get(db + fb + tb, &blob));
-      d_descs = reinterpret_cast<JoinDesc*>(blob);
-      d_first = reinterpret_cast<uint64_t*>(blob + db);
-      d_tail = reinterpret_cast<uint64_t*>(blob + db + fb);
-      status = reinterpret_cast<uint32_t*>(d_tail);
-    }
+    MQ_TRY(ensure_blob());
     blob_host.assign(db + fb + tb, 0);
     memcpy(blob_host.data(), descs.data(), db);
     memcpy(blob_host.data() + db, first.data(), fb);
@@ -1425,7 +1430,12 @@ struct BatchJoin {
 
   int count() {
     MQ_TRY(size_tables());
+    MQ_TRY(ensure_blob());
+    // a retry rebuilds the tables in place of the first attempt's (a fixed
+    // scratch array would otherwise hold both sets)
+    const auto mark = mem->mark();
     for (int attempt = 0;; ++attempt) {
+      if (attempt) mem->rewind(mark);
       MQ_TRY(allocate());
       MQ_TRY(count_phases());  // its upload zeroes the status word
       // one copy: status word, work counter, row counts
@@ -1636,6 +1646,7 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 constexpr uint64_t kNoAllocMaxBuild = uint64_t(1) << 18;  // rows of the smaller input
 constexpr uint64_t kNoAllocMaxProbe = uint64_t(1) << 20;  // rows of the larger input
+constexpr uint64_t kNoAllocMaxRows = uint64_t(1) << 32;   // output rows
 constexpr int kNoAllocMaxDevices = 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -1664,6 +1675,8 @@ int noalloc_scratch(unsigned char** out) {
 struct Carve {
   unsigned char* base;
   size_t used = 0;
+  size_t mark() const { return used; }
+  void rewind(size_t m) { used = m; }  // the stream has finished with everything past m
   template <class T>
   int get(size_t count, T** out) {
     size_t bytes = (std::max<size_t>(count * sizeof(T), 16) + 255) & ~size_t(255);
@@ -1684,15 +1697,20 @@ extern "C" int mapsq_join_noalloc(const mapsq_table* left, const mapsq_table* ri
                                   uint64_t out_capacity_rows, mapsq_table* out, uint64_t* out_rows,
                                   void* cuda_stream) {
   if (!left || !right || !out || !out_rows) return MAPSQ_ERR_INVALID;
+  // the limits hold for the smaller and the larger input, checked before any device work
+  const uint64_t n_small = std::min(left->nrows, right->nrows), n_large = std::max(left->nrows, right->nrows);
+  if (n_small > kNoAllocMaxBuild || n_large > kNoAllocMaxProbe) return MAPSQ_ERR_INVALID;  // beyond the scratch array
   unsigned char* base = nullptr;
   MQ_TRY(noalloc_scratch(&base));
   Carve carve{base};
   uint32_t* status = nullptr;
   MQ_TRY(carve.get(64, &status));
   BatchJoin<Carve> bj{nullptr, static_cast<cudaStream_t>(cuda_stream), status, &carve};
+  // always the hash build on the smaller input: the sorted join would build on
+  // a larger, key-sorted side, which the limits above do not cover
+  bj.algorithm = MAPSQ_JOIN_HASH;
   MQ_TRY(bj.prepare(1, &left, &right));
   const JoinPlan& pl = bj.plans[0];
-  if (pl.nb > kNoAllocMaxBuild || pl.np > kNoAllocMaxProbe) return MAPSQ_ERR_INVALID;  // beyond the scratch array
   const int ncols = pl.lay.ncols;
   if (ncols && !out_cols) return MAPSQ_ERR_INVALID;
   for (int c = 0; c < ncols; ++c)
@@ -1700,6 +1718,7 @@ extern "C" int mapsq_join_noalloc(const mapsq_table* left, const mapsq_table* ri
   MQ_TRY(bj.count());
   *out_rows = pl.T;
   if (pl.T > out_capacity_rows) return MAPSQ_ERR_BUDGET;
+  if (pl.T > kNoAllocMaxRows) return MAPSQ_ERR_UNSUPPORTED;  // its write partition would not fit in the array
   memset(out, 0, sizeof(*out));
   out->nrows = pl.T;
   out->ncols = uint32_t(ncols);
