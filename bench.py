@@ -1,12 +1,16 @@
 """Benchmark of the MapSQ join path on GB300.
 
-Default workload: plain BGP evaluation over a seeded university-shaped graph of
-1e7 triples, 32 star and chain BGPs of 3-6 patterns (one step = every BGP
-evaluated once through ``mapsq_query``: pattern scans, joins, result tables).
-Metric: output bindings/s (one binding = one solution row of a BGP).
+Default workload: the skewed large join, A = 2^26 rows x B = 2^24 rows of four
+uint32 columns, two shared variables packed into a 64-bit key, Zipf(1.1) key
+frequencies on A, exactly 2^28 output rows (one step = one mapsq_join).
+Metric: output bindings/s (one binding = one output row).  After the headline,
+the same line carries the other join workloads measured in the same process
+(``other_workloads``): the 256-join uneven batch (batched against plain), the
+32 BGPs over a 1e7-triple university graph (plain against batched) and the
+16384 x 8192 pairwise join.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload university_bgp|skewed_join|pairwise_uniform|uneven_batch|serving]
+                  [--workload skewed_join|university_bgp|pairwise_uniform|uneven_batch|serving]
 
 ``--impl reference`` times the CPU oracle on the host cores (one process per
 core) on bounded samples of the same workload per step (the paper has no code
@@ -14,11 +18,11 @@ to run).
 Under torchrun (N > 1) every rank evaluates the whole workload on its own GPU
 (independent replicas; weak scaling, no collective on the data path).
 
-Other workloads: ``skewed_join`` (one 2^26 x 2^24 join, Zipf 1.1 on a 64-bit
-key), ``pairwise_uniform`` (16384 x 8192), ``uneven_batch`` (256 joins of
-uneven size in one mapsq_join_batch, against the same joins one by one) and
-``serving`` (a Poisson stream of 2000 queries/s over 1e8 triples through the
-serving loop; p50/p99 latency, against serial mapsq_query).
+Other workloads alone: ``university_bgp`` (32 BGPs through mapsq_query, against
+mapsq_query_batch), ``pairwise_uniform`` (16384 x 8192), ``uneven_batch`` (256
+joins of uneven size in one mapsq_join_batch, against the same joins one by
+one) and ``serving`` (a Poisson stream of 2000 queries/s over 1e8 triples
+through the serving loop; p50/p99 latency, against serial mapsq_query).
 """
 from __future__ import annotations
 
@@ -50,9 +54,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)  # at least 2: the last one is profiled
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="university_bgp",
+    ap.add_argument("--workload", default="skewed_join",
                     choices=["university_bgp", "skewed_join", "pairwise_uniform", "uneven_batch", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skewed_join only: skip the other workloads measured after the headline")
     ap.add_argument("--sorted-ratio", type=int, default=0,
                     help="fix the hash-vs-sorted crossover instead of autotuning it (profiler captures)")
     ap.add_argument("--size", default="full", choices=["full", "small"],
@@ -95,6 +101,17 @@ PINNED = Pinned()
 class Workload:
     name = ""
     config = {}
+    oracle_unit = "units"
+
+    def release(self, ctx):
+        """Free the workload's device tables."""
+        for key in ("tA", "tB", "tL", "tR"):
+            t = self.__dict__.pop(key, None)
+            if t is not None:
+                t.free()
+        for a, b in self.__dict__.pop("dev", []):
+            a.free()
+            b.free()
 
     def setup_gpu(self, ctx):
         pass
@@ -114,6 +131,7 @@ class Workload:
 
 class UniversityBGP(Workload):
     name = "university_bgp"
+    oracle_unit = "whole BGPs"
 
     def __init__(self, n_triples=10_000_000, n_bgps=32, seed=2):
         self.s, self.p, self.o = gen.university_graph(n_triples, seed=seed)
@@ -177,6 +195,7 @@ class UniversityBGP(Workload):
 
 class SkewedJoin(Workload):
     name = "skewed_join"
+    oracle_unit = "key buckets: the rows of A and B whose x has the same top 10 bits, joined"
 
     def __init__(self, log_a=26, log_b=24, log_keys=22):
         self.A, self.B = gen.skewed_two_key(seed=3, log_a=log_a, log_b=log_b, log_keys=log_keys)
@@ -210,16 +229,38 @@ class SkewedJoin(Workload):
             x.free()
         return n, h2d, d2h
 
+    def alg_bytes(self, rows):
+        """Compulsory bytes of one join: both inputs read once, the output written once."""
+        return 4 * (self.A.nrows * 4 + self.B.nrows * 4) + 4 * rows * 6
+
+    ORACLE_BUCKETS = 1024  # oracle units: the keys whose x has the same top 10 bits
+
     def run_oracle(self, sample_index, budget_s=2.0):
+        """The oracle on one key bucket: the rows of A and B whose keys fall in
+        it, joined (the bucket's share of the whole join's output)."""
         import oracle
-        n = 1 << 18
-        lo = (sample_index * n) % self.A.nrows
-        A = gen.Table(self.A.vars, [c[lo:lo + n] for c in self.A.cols])
-        return oracle.join_mapreduce(A, self.B)[1].shape[0], n
+        if not hasattr(self, "_parts"):  # rows grouped by bucket, once (not timed)
+            nb = self.ORACLE_BUCKETS
+            shift = np.uint32(32 - int(np.log2(nb)))
+            self._parts = []
+            for T in (self.A, self.B):
+                b = (T.cols[0] >> shift).astype(np.uint16)
+                order = np.argsort(b, kind="stable")  # a radix sort for 16-bit keys
+                cut = np.searchsorted(b[order], np.arange(nb + 1))
+                self._parts.append((T, [c[order] for c in T.cols], cut))
+        k = sample_index % self.ORACLE_BUCKETS
+        (TA, ca, cuta), (TB, cb, cutb) = self._parts
+        A = gen.Table(TA.vars, [c[cuta[k]:cuta[k + 1]] for c in ca])
+        B = gen.Table(TB.vars, [c[cutb[k]:cutb[k + 1]] for c in cb])
+        return oracle.join_mapreduce(A, B)[1].shape[0], 1
 
 
 class PairwiseUniform(Workload):
     name = "pairwise_uniform"
+    oracle_unit = "whole joins"
+
+    def alg_bytes(self, rows):
+        return 4 * (self.L.nrows * 2 + self.R.nrows * 2) + 12 * rows
 
     def __init__(self):
         self.L, self.R = gen.pairwise_uniform(seed=1)
@@ -262,6 +303,13 @@ class UnevenBatch(Workload):
     joins); the alternative form runs the same joins one ``mapsq_join`` after
     another."""
     name = "uneven_batch"
+    oracle_unit = "whole joins"
+
+    def alg_bytes(self, rows):
+        """Compulsory bytes of the batch: every input read once, every output
+        written once (output bytes of the last step)."""
+        ins = sum(4 * (L.nrows * len(L.cols) + R.nrows * len(R.cols)) for L, R in self.joins)
+        return ins + getattr(self, "out_bytes", 0)
 
     def __init__(self, seed=4, n_joins=256, log_hi=22.0):
         self.joins = [(L, R) for L, R, _ in gen.uneven_batch(seed=seed, n_joins=n_joins, log_hi=log_hi)]
@@ -276,10 +324,12 @@ class UnevenBatch(Workload):
                      ctx.table(R.vars, [torch.from_numpy(c).cuda() for c in R.cols])) for L, R in self.joins]
 
     def run_gpu(self, ctx):
-        rows = 0
+        rows = out = 0
         for t in ctx.join_batch([a for a, _ in self.dev], [b for _, b in self.dev]):
             rows += t.nrows
+            out += 4 * t.nrows * len(t.vars)
             t.free()
+        self.out_bytes = out
         return rows
 
     def run_gpu_alt(self, ctx):
@@ -333,6 +383,7 @@ class Serving(UniversityBGP):
     the library's serving loop with continuous batching and a 40 GB budget for
     the tables in flight.  One step = ``step_s`` seconds of arrivals."""
     name = "serving"
+    oracle_unit = "queries of the stream"
 
     def __init__(self, n_triples=100_000_000, pool=2048, seed=5, rate=2000.0, step_s=1.5, budget=40 << 30):
         self.s, self.p, self.o = gen.university_graph(n_triples, seed=2)
@@ -699,6 +750,89 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(w, ctx, fn, steps, flush, stream):
+    """``steps`` calls of ``fn(ctx)``, each bracketed by CUDA events on the
+    context's stream, the L2 flushed before each (outside the events).  Returns
+    (total ms, rows, per-step ms)."""
+    import torch
+    total_ms, rows, step_ms = 0.0, 0, []
+    for _ in range(steps):
+        flush.fill_(1)  # evict the L2 between timed steps (not timed)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rows += fn(ctx)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        total_ms += step_ms[-1]
+    return total_ms, rows, step_ms
+
+
+def kernel_roofline(ctx, w, fn, steps, flush, stream, peak, peak_kind):
+    """The dominant kernel's roofline, measured in its own pass after the timed
+    steps: one step profiled in full names the kernel with the most device time,
+    then ``steps`` steps time that kernel alone (CUDA events around each of its
+    launches, on the launching stream).  Returns (roofline, per-kernel table of
+    the fully profiled step)."""
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    fn(ctx)
+    full = ctx.kernel_stats()
+    ctx.set_profiling(False)
+    if not full:
+        return None, {}
+    dominant = max(full.items(), key=lambda kv: kv[1]["device_ms"])[0]
+    ctx.reset_stats()
+    ctx.profile_only(dominant)
+    ctx.set_profiling(True)
+    timed_steps(w, ctx, fn, steps, flush, stream)
+    st = ctx.kernel_stats()[dominant]
+    ctx.set_profiling(False)
+    ctx.profile_only(None)
+    per_launch_s = st["device_ms"] / 1000.0 / st["launches"]
+    achieved = st["alg_bytes"] / st["launches"] / per_launch_s / 1e9
+    total = sum(v["device_ms"] for v in full.values())
+    roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+            "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(dominant, w.name), "launches": st["launches"],
+            "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
+            "ms_per_launch": per_launch_s * 1000.0, "share_of_device_time": full[dominant]["device_ms"] / total}
+    table = {k: {"launches": v["launches"], "ms": round(v["device_ms"], 4)} for k, v in full.items()}
+    return roof, table
+
+
+def measure(ctx, w, args, flush, stream, peak, peak_kind, steps, e2e_steps):
+    """One workload of the line's ``other_workloads``: warm-up, ``steps`` timed
+    steps, then the passes of ``measure_rest``."""
+    import torch
+    for _ in range(args.warmup):
+        w.run_gpu(ctx)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    total_ms, rows, step_ms = timed_steps(w, ctx, w.run_gpu, steps, flush, stream)
+    launches = ctx.launch_count() - launches0
+    res = {"value": rows / (total_ms / 1000.0), "unit": UNIT, "ms_per_step": total_ms / steps,
+           "rows_per_step": rows / steps, "step_ms_p50": float(np.percentile(step_ms, 50)),
+           "step_ms_p99": float(np.percentile(step_ms, 99)), "gpu_launches": launches}
+    if hasattr(w, "alg_bytes"):
+        res["roofline_whole_step"] = whole_step_roofline(w, rows / steps, total_ms / steps, peak)
+    res.update(measure_rest(ctx, w, steps, e2e_steps, flush, stream, peak, peak_kind))
+    return res
+
+
+def whole_step_roofline(w, rows_per_step, ms_per_step, peak):
+    alg = w.alg_bytes(rows_per_step)
+    achieved = alg / (ms_per_step / 1000.0) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "alg_bytes_per_step": alg,
+            "what": "compulsory bytes of the whole step (inputs read once, output written once) / step time, "
+                    "every kernel included"}
+
+
+EXTRAS = ("uneven_batch", "university_bgp", "pairwise_uniform")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -711,6 +845,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     w = make_workload(args)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    peak, peak_kind = measured_peaks()
 
     def barrier():
         if world > 1:
@@ -720,74 +855,32 @@ def run_ours(args):
         w.setup_gpu(ctx)
         tune = tuned(ctx, args)
         stream = torch.cuda.current_stream(dev)
-        for _ in range(args.warmup - 1):
+        for _ in range(args.warmup):
             w.run_gpu(ctx)
-        # last warm-up step profiled in full: it names the kernel with the most device time
-        ctx.reset_stats()
-        ctx.set_profiling(True)
-        w.run_gpu(ctx)
-        warm_stats = ctx.kernel_stats()
-        ctx.set_profiling(False)
-        dominant = max(warm_stats.items(), key=lambda kv: kv[1]["device_ms"])[0] if warm_stats else None
-        torch.cuda.synchronize()
-        # the timed region brackets only the dominant kernel's launches with events
-        ctx.reset_stats()
-        ctx.profile_only(dominant)
-        ctx.set_profiling(True)
         launches0 = ctx.launch_count()
         barrier()
         torch.cuda.synchronize()
-        total_ms, rows, step_ms = 0.0, 0, []
         with ClockSampler(local) as clocks:
-            for _ in range(args.steps):
-                flush.fill_(1)  # evict the L2 between timed steps (not timed)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                rows += w.run_gpu(ctx)
-                b.record(stream)
-                b.synchronize()
-                step_ms.append(a.elapsed_time(b))
-                total_ms += step_ms[-1]
+            total_ms, rows, step_ms = timed_steps(w, ctx, w.run_gpu, args.steps, flush, stream)
         torch.cuda.synchronize()
         barrier()
         launches = ctx.launch_count() - launches0
-        stats = ctx.kernel_stats()
-        ctx.set_profiling(False)
-        ctx.profile_only(None)
-
-        # the other form of the same step (batched or plain), when the workload has one
-        batched = None
-        if hasattr(w, "run_gpu_alt"):
-            for _ in range(2):
-                w.run_gpu_alt(ctx)
-            bms, brows = 0.0, 0
-            for _ in range(args.steps):
-                flush.fill_(1)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                brows += w.run_gpu_alt(ctx)
-                b.record(stream)
-                b.synchronize()
-                bms += a.elapsed_time(b)
-            batched = {"value": brows / (bms / 1000.0), "unit": UNIT, "ms_per_step": bms / args.steps,
-                       "form": w.alt_form}
-
-        # end to end through the C ABI with host buffers
-        for _ in range(2):
-            w.run_e2e(ctx)
-        torch.cuda.synchronize()
-        e_rows, h2d, d2h = 0, 0, 0
-        t0 = time.perf_counter()
-        e_steps = max(1, min(args.steps, 5))
-        for _ in range(e_steps):
-            r, hi, ho = w.run_e2e(ctx)
-            e_rows += r
-            h2d += hi
-            d2h += ho
-        torch.cuda.synchronize()
-        e_dt = time.perf_counter() - t0
+        head = measure_rest(ctx, w, args.steps, max(1, min(args.steps, 5)), flush, stream, peak, peak_kind)
+        extras = {}
+        if args.workload == "skewed_join" and args.size == "full" and not args.no_extras and world == 1:
+            w.release(ctx)
+            for name in EXTRAS:
+                x = WORKLOADS[name]()
+                x.setup_gpu(ctx)
+                r = measure(ctx, x, args, flush, stream, peak, peak_kind, steps=min(args.steps, 10),
+                            e2e_steps=2)
+                r["config"] = x.config
+                for k in ("total_ms", "rows"):
+                    r.pop(k, None)
+                if "other_form" in r:
+                    r["other_over_this"] = r["other_form"]["value"] / r["value"]
+                extras[name] = r
+                x.release(ctx)
 
     t_max, rows_all = combine_ranks(total_ms, rows, world, dev)
     if world > 1:
@@ -795,38 +888,32 @@ def run_ours(args):
     if rank != 0:
         return
     value = rows_all / (t_max / 1000.0)
-    peak, peak_kind = measured_peaks()
-    dom = max(stats.items(), key=lambda kv: kv[1]["device_ms"]) if stats else None
-    roofline = None
-    if dom:
-        name, st = dom
-        per_launch_s = st["device_ms"] / 1000.0 / st["launches"]
-        achieved = st["alg_bytes"] / st["launches"] / per_launch_s / 1e9
-        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                    "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": ncu_traffic(name, w.name), "launches": st["launches"],
-                    "alg_bytes_per_launch": st["alg_bytes"] / st["launches"],
-                    "share_of_device_time": warm_stats[name]["device_ms"] / sum(v["device_ms"]
-                                                                                for v in warm_stats.values())}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": w.config,
             "rows_per_step": rows / args.steps,
             "step_ms_p50": float(np.percentile(step_ms, 50)), "step_ms_p99": float(np.percentile(step_ms, 99)),
-            "e2e": {"value": e_rows / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d // e_steps,
-                    "d2h_bytes_per_step": d2h // e_steps},
-            "gpu_launches": launches, "roofline": roofline, "clocks": clocks.summary(), "other_form": batched,
-            "store_build": ({"seconds": w.store_build_s, "triples_per_s": len(w.s) / w.store_build_s}
-                            if hasattr(w, "store_build_s") else None),
-            "autotune": {"sorted_ratio": tune["sorted_ratio"],
-                         "points": [(p["ratio"], round(p["hash_ms"], 3), round(p["sorted_ms"], 3))
-                                    for p in tune["points"]]},
-            "kernels_last_warmup_step": {k: {"launches": v["launches"], "ms": round(v["device_ms"], 4)}
-                                         for k, v in warm_stats.items()}}
+            "e2e": head["e2e"], "gpu_launches": launches, "roofline": head["roofline"],
+            "clocks": clocks.summary()}
+    if hasattr(w, "alg_bytes"):
+        line["roofline_whole_step"] = whole_step_roofline(w, rows / args.steps, t_max / args.steps, peak)
+    if "other_form" in head:
+        line["other_form"] = head["other_form"]
+    line.update({
+        "store_build": ({"seconds": w.store_build_s, "triples_per_s": len(w.s) / w.store_build_s}
+                        if hasattr(w, "store_build_s") else None),
+        "autotune": {"sorted_ratio": tune["sorted_ratio"],
+                     "points": [(p["ratio"], round(p["hash_ms"], 3), round(p["sorted_ms"], 3))
+                                for p in tune["points"]]},
+        "kernels_one_step": head["kernels_one_step"]})
+    if extras:
+        line["other_workloads"] = extras
     if not args.no_cpu_baseline and world == 1:
         t0 = time.perf_counter()
         crow, cunits = 0, 0
         k = 0
+        w.run_oracle(0, budget_s=0.0)  # one-off setup of the oracle's inputs, not timed
+        t0 = time.perf_counter()
         while time.perf_counter() - t0 < 15.0:
             r, u = w.run_oracle(k, budget_s=15.0 - (time.perf_counter() - t0))
             crow += r
@@ -834,13 +921,45 @@ def run_ours(args):
             k += u
         cdt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": crow / cdt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{cunits} units of the {w.name} workload (BGPs or join slices) in "
+                                "sample": f"{cunits} units of the {w.name} workload ({w.oracle_unit}) in "
                                           f"{cdt:.1f} s, numpy oracle, single thread"}
         v, cores, units = oracle_all_cores(args)
         line["cpu_baseline_all_cores"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                          "sample": f"{units} units of the {w.name} workload, one spawned process "
-                                                    f"per core for about 10 s each"}
+                                          "sample": f"{units} units of the {w.name} workload ({w.oracle_unit}), "
+                                                    f"one spawned process per core for about 10 s each"}
     print(json.dumps(line), flush=True)
+
+
+def measure_rest(ctx, w, steps, e2e_steps, flush, stream, peak, peak_kind):
+    """After a workload's timed steps, each in its own pass: the other form
+    (batched or plain) when the workload has one, end to end through host
+    buffers, and the dominant kernel's roofline."""
+    import torch
+    res = {}
+    if hasattr(w, "run_gpu_alt"):
+        for _ in range(2):
+            w.run_gpu_alt(ctx)
+        bms, brows, bstep = timed_steps(w, ctx, w.run_gpu_alt, steps, flush, stream)
+        res["other_form"] = {"value": brows / (bms / 1000.0), "unit": UNIT, "ms_per_step": bms / steps,
+                             "step_ms_p50": float(np.percentile(bstep, 50)),
+                             "step_ms_p99": float(np.percentile(bstep, 99)), "form": w.alt_form}
+    for _ in range(2):
+        w.run_e2e(ctx)
+    torch.cuda.synchronize()
+    e_rows, h2d, d2h = 0, 0, 0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r, hi, ho = w.run_e2e(ctx)
+        e_rows += r
+        h2d += hi
+        d2h += ho
+    torch.cuda.synchronize()
+    e_dt = time.perf_counter() - t0
+    res["e2e"] = {"value": e_rows / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
+                  "d2h_bytes_per_step": d2h // e2e_steps}
+    res["roofline"], res["kernels_one_step"] = kernel_roofline(ctx, w, w.run_gpu, steps, flush, stream,
+                                                               peak, peak_kind)
+    return res
 
 
 def run_serving(args):
@@ -864,9 +983,6 @@ def run_serving(args):
         warm_stats = ctx.kernel_stats()
         ctx.set_profiling(False)
         dominant = max(warm_stats.items(), key=lambda kv: kv[1]["device_ms"])[0] if warm_stats else None
-        ctx.reset_stats()
-        ctx.profile_only(dominant)
-        ctx.set_profiling(True)
         launches0 = ctx.launch_count()
         if world > 1:
             dist.barrier()
@@ -875,6 +991,11 @@ def run_serving(args):
             rows, wall, dev_ms, _, _, counters, idx = w.serve(ctx, args.steps, part=2)
         torch.cuda.synchronize()
         launches = ctx.launch_count() - launches0
+        # the dominant kernel timed alone, on a separate stream of arrivals after the timed one
+        ctx.reset_stats()
+        ctx.profile_only(dominant)
+        ctx.set_profiling(True)
+        w.serve(ctx, max(1, args.warmup // 2), part=4)
         stats = ctx.kernel_stats()
         ctx.set_profiling(False)
         ctx.profile_only(None)

@@ -41,3 +41,51 @@ def join_and_check(ctx, L, R, what="", opts=None):
         out.free()
         tl.free()
         tr.free()
+
+
+def sort_rows_device(rows):
+    """Rows of a (n, c) int32 device tensor holding uint32 values, in
+    lexicographic uint32 order (stable LSD passes of torch.sort over 64-bit
+    keys packing two columns each; a permutation of the rows, so it cannot make
+    two different multisets equal)."""
+    import torch
+    n, c = rows.shape
+    if n == 0 or c == 0:
+        return rows
+    perm = torch.arange(n, device=rows.device)
+    for a in reversed(range(0, c, 2)):
+        # the high column with its top bit flipped is in signed order, so
+        # hi * 2^32 + lo (lo as an unsigned value) orders the pair and never overflows
+        k = (rows[:, a] ^ -(1 << 31)).to(torch.int64) * (1 << 32)
+        if a + 1 < c:
+            k = k + (rows[:, a + 1].to(torch.int64) & 0xFFFFFFFF)
+        _, idx = torch.sort(k[perm], stable=True)
+        perm = perm[idx]
+        del k, idx
+    return rows[perm]
+
+
+def assert_rows_equal_device(got, want_rows, what=""):
+    """``got``: (n, c) int32 device tensor of output rows (uint32 values) with
+    the columns in the oracle's order; ``want_rows``: the oracle's (n, c) uint32
+    rows.  Compares the two canonically sorted multisets element by element."""
+    import torch
+    want = torch.from_numpy(np.ascontiguousarray(want_rows).view(np.int32)).to(got.device)
+    assert got.shape == want.shape, f"{what}: {tuple(got.shape)} rows x cols, expected {tuple(want.shape)}"
+    if got.shape[0] == 0:
+        return
+    g, w = sort_rows_device(got), sort_rows_device(want)
+    bad = torch.nonzero(torch.any(g != w, dim=1)).flatten()
+    if bad.numel():
+        i = int(bad[0])
+        raise AssertionError(f"{what}: {bad.numel()} rows differ, first at {i}: "
+                             f"{g[i].cpu().numpy().view(np.uint32)} vs {w[i].cpu().numpy().view(np.uint32)}")
+
+
+def oracle_pool(processes=None, initializer=None, initargs=()):
+    """A pool of spawned host processes for oracle work (the test process has a
+    CUDA context, so workers are spawned, never forked)."""
+    import multiprocessing as mp
+    import os
+    n = processes or max(1, min(16, os.cpu_count() or 1))
+    return mp.get_context("spawn").Pool(n, initializer=initializer, initargs=initargs)

@@ -1,163 +1,142 @@
-"""Parity at the full size of the skewed large join: A = 2^26 rows, B = 2^24 rows,
-two shared variables packed in a 64-bit key, Zipf(1.1) key frequencies on A,
-exactly 2^28 output rows.  The oracle cannot materialise 2^28 rows in seconds,
-so the test checks (1) the exact row count, (2) the count of output rows of
-every key against |A_k| * |B_k| from independent histograms, and (3) every
-output row of a seeded sample of keys (the hottest included) against the
-oracle's join restricted to those keys."""
+"""Parity at full size, every output row against the oracle.
+
+* Skewed large join: A = 2^26 rows, B = 2^24 rows, two shared variables packed
+  in a 64-bit key, Zipf(1.1) key frequencies on A, exactly 2^28 output rows.
+  The key space is cut into 16 buckets (top four bits of x); per bucket the
+  oracle joins the bucket's rows of A and B (Algorithm 1 restricted to those
+  keys, so the buckets' results add up to the whole join) and the GPU rows of
+  that bucket are compared with it as canonically sorted multisets.
+* Uneven batch: all 256 joins of the batch, each compared in full.
+* Serving: every distinct query of a served stream over the 1e8-triple graph
+  equals the oracle's evaluation of it, and every served result equals the
+  same query evaluated alone.
+
+The oracle runs in spawned host processes meanwhile; the canonical sort of
+large results runs on the device through torch.sort (a permutation of the
+rows, which cannot make different multisets equal)."""
 import numpy as np
 import pytest
 
 import gen
 import oracle
-from gpu_helpers import assert_same_multiset
+import oracle_jobs
+from gpu_helpers import assert_rows_equal_device, oracle_pool
 
 pytestmark = pytest.mark.gpu
 
 
-def _u64(col):
+def _as_u64(col):
     import torch
     return col.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
 
 
-def _packed(x, y):
-    return (x.astype(np.uint64) << np.uint64(32)) | y.astype(np.uint64)
+def _rows(cols, sel=None):
+    import torch
+    parts = [c.view(torch.int32) if sel is None else c.view(torch.int32)[sel] for c in cols]
+    return torch.stack(parts, dim=1)
 
 
 def test_skewed_join_full_size():
     import torch
     from paper_1702_03484_gb300 import Context
     A, B = gen.skewed_two_key(seed=3)
-    with Context(device=0) as ctx:
+    buckets, shift = 16, np.uint32(28)
+    ab, bb = A.cols[0] >> shift, B.cols[0] >> shift
+    jobs = [((A.vars, [c[ab == b] for c in A.cols]), (B.vars, [c[bb == b] for c in B.cols])) for b in range(buckets)]
+    with oracle_pool(8) as pool, Context(device=0) as ctx:
+        wants = pool.imap(oracle_jobs.join_job, jobs)
         tA = ctx.table(A.vars, [torch.from_numpy(c).cuda() for c in A.cols])
         tB = ctx.table(B.vars, [torch.from_numpy(c).cuda() for c in B.cols])
         out = ctx.join(tA, tB)
         assert out.nrows == 1 << 28
         assert out.vars == [0, 1, 2, 3, 4, 5]
         cols = out.device_columns()
-        key = (_u64(cols[0]) << 32) | _u64(cols[1])
-        uk, cnt = torch.unique(key, return_counts=True)
-        uk, cnt = uk.cpu().numpy().view(np.uint64), cnt.cpu().numpy()
-        order = np.argsort(uk, kind="stable")  # torch orders the keys as signed int64
-        uk, cnt = uk[order], cnt[order]
-
-        ka, ca = np.unique(_packed(A.cols[0], A.cols[1]), return_counts=True)
-        kb, cb = np.unique(_packed(B.cols[0], B.cols[1]), return_counts=True)
-        common, ia, ib = np.intersect1d(ka, kb, assume_unique=True, return_indices=True)
-        keep = ca[ia] * cb[ib] > 0
-        assert np.array_equal(uk, common[keep])
-        assert np.array_equal(cnt, (ca[ia] * cb[ib])[keep])
-
-        # every row of a sample of keys, the hottest key included
-        r = gen.Rng(31)
-        sample = np.unique(np.concatenate((ka[np.argsort(-ca)[:1]], ka[r.below(24, ka.shape[0])])))
-        sel = torch.isin(key, torch.from_numpy(sample.astype(np.int64)).cuda())
-        got_rows = torch.stack([c.view(torch.int32)[sel] for c in cols], dim=1).cpu().numpy().view(np.uint32)
-        ma = np.isin(_packed(A.cols[0], A.cols[1]), sample)
-        mb = np.isin(_packed(B.cols[0], B.cols[1]), sample)
-        As = gen.Table(A.vars, [c[ma] for c in A.cols])
-        Bs = gen.Table(B.vars, [c[mb] for c in B.cols])
-
-        class Rows:
-            nrows = got_rows.shape[0]
-
-            @staticmethod
-            def to_host():
-                return out.vars, [np.ascontiguousarray(got_rows[:, c]) for c in range(6)]
-
-        assert_same_multiset(Rows, oracle.join_mapreduce(As, Bs), "sampled keys")
+        xb = _as_u64(cols[0]) >> 28
+        checked = 0
+        for b, (wv, wr) in enumerate(wants):
+            assert wv == out.vars
+            got = _rows(cols, xb == b)
+            assert_rows_equal_device(got, wr, f"key bucket {b}")
+            checked += got.shape[0]
+            del got
+        assert checked == 1 << 28
+        out.free()
 
 
 def test_uneven_batch_full_size():
-    """The 256-join batch at full size through mapsq_join_batch: every join's row
-    count against the cardinality identity from independent histograms; joins of
-    up to 2^18 rows in full against the oracle, larger ones on a sample of keys
-    (the hottest key of the left side included)."""
+    """The 256-join batch at full size through mapsq_join_batch: every join
+    compared in full with the oracle."""
     import torch
     from paper_1702_03484_gb300 import Context
     joins = gen.uneven_batch(seed=4)
-    r = gen.Rng(41)
-    with Context(device=0) as ctx:
+    jobs = [((L.vars, L.cols), (R.vars, R.cols)) for L, R, _ in joins]
+    with oracle_pool() as pool, Context(device=0) as ctx:
+        wants = pool.imap(oracle_jobs.join_job, jobs)
         dev = [(ctx.table(L.vars, [torch.from_numpy(c).cuda() for c in L.cols]),
                 ctx.table(R.vars, [torch.from_numpy(c).cuda() for c in R.cols])) for L, R, _ in joins]
         outs = ctx.join_batch([a for a, _ in dev], [b for _, b in dev])
         assert len(outs) == len(joins)
-        for j, ((L, R, s), out) in enumerate(zip(joins, outs)):
-            kl, cl = np.unique(L.cols[0], return_counts=True)
-            kr, cr = np.unique(R.cols[0], return_counts=True)
-            _, il, ir = np.intersect1d(kl, kr, assume_unique=True, return_indices=True)
-            assert out.nrows == int((cl[il].astype(np.int64) * cr[ir]).sum()), f"join {j} (s={s})"
-            if out.nrows <= 1 << 18:
-                assert_same_multiset(out, oracle.join_mapreduce(L, R), f"join {j}")
-            else:
-                common = kl[il]
-                sample = np.unique(np.concatenate((kl[np.argsort(-cl)[:1]], common[r.below(6, common.shape[0])])))
-                key_col = out.device_columns()[out.vars.index(0)]
-                sel = torch.isin(key_col.view(torch.int32), torch.from_numpy(sample.view(np.int32)).cuda())
-                got = torch.stack([c.view(torch.int32)[sel] for c in out.device_columns()], dim=1)
-                got = got.cpu().numpy().view(np.uint32)
-                Ls = gen.Table(L.vars, [c[np.isin(L.cols[0], sample)] for c in L.cols])
-                Rs = gen.Table(R.vars, [c[np.isin(R.cols[0], sample)] for c in R.cols])
-
-                class Rows:
-                    nrows = got.shape[0]
-
-                    @staticmethod
-                    def to_host():
-                        return out.vars, [np.ascontiguousarray(got[:, c]) for c in range(got.shape[1])]
-
-                assert_same_multiset(Rows, oracle.join_mapreduce(Ls, Rs), f"join {j}, sampled keys")
+        total = 0
+        for j, ((L, R, s), out, (wv, wr)) in enumerate(zip(joins, outs, wants)):
+            assert out.vars == wv, f"join {j}"
+            assert out.nrows == wr.shape[0], f"join {j} (s={s})"
+            if out.nrows:
+                assert_rows_equal_device(_rows(out.device_columns()), wr, f"join {j} (s={s})")
+            total += out.nrows
             out.free()
+        assert total > 1 << 27
 
 
-def test_served_stream_full_size():
-    """Serving over the 1e8-triple graph: a burst of the Poisson stream's queries
-    is served concurrently; every result equals the same query evaluated alone
-    through mapsq_query, and a sample of the smaller ones equals the oracle."""
+def test_served_stream_full_size(tmp_path):
+    """Serving over the 1e8-triple graph: 400 arrivals at about 2000 queries/s
+    drawn from 128 witness BGPs are served concurrently; every served result
+    equals the same query evaluated alone through mapsq_query, and every
+    distinct query's result equals the oracle's."""
     import time
     from paper_1702_03484_gb300 import Context
     from gen.bgp import GraphIndex, generate_bgps
     from gpu_helpers import host_rows
     s, p, o = gen.university_graph(100_000_000, seed=2)
-    bgps = [b["patterns"] for b in generate_bgps(GraphIndex(s, p, o), 256, seed=5, k_range=(3, 8),
+    bgps = [b["patterns"] for b in generate_bgps(GraphIndex(s, p, o), 128, seed=5, k_range=(3, 8),
                                                  var_range=None)]
     r = gen.Rng(5, 7)
-    stream = [bgps[int(i)] for i in r.below(400, len(bgps))]
-    with Context(device=0) as ctx:
-        ctx.load_triples(s, p, o)
-        ctx.serve_start(max_active=256, mem_budget_bytes=40 << 30)
-        tickets = []
-        for b in stream:
-            tickets.append(ctx.submit(b))
-            time.sleep(0.0005)  # 2000 queries/s
-        served = [None] * len(stream)
-        deadline = time.time() + 300
-        while any(x is None for x in served) and time.time() < deadline:
-            for i, t in enumerate(tickets):
-                if served[i] is None:
-                    res = ctx.poll(t)
-                    if res is not None:
-                        served[i] = oracle.canonical(host_rows(res))
-                        res.free()
-            time.sleep(0.001)
-        stats = ctx.serve_stats()
-        ctx.serve_stop()
-        assert all(x is not None for x in served)
-        assert stats["completed"] == len(stream) and stats["failed"] == 0
-        alone = {}
-        for i, b in enumerate(stream):
-            key = str(b)
-            if key not in alone:
-                res = ctx.query(b)
-                alone[key] = (oracle.canonical(host_rows(res)), res.nrows)
-                res.free()
-            want = alone[key][0]
-            assert served[i][0] == want[0] and np.array_equal(served[i][1], want[1]), b
+    stream = [int(i) for i in r.below(400, len(bgps))]
+    distinct = sorted(set(stream))
     G = oracle.distinct_triples(s, p, o)
-    small = sorted((k for k in alone if alone[k][1] > 0), key=lambda k: alone[k][1])[:4]
-    assert small
-    for key in small:
-        b = next(x for x in stream if str(x) == key)
-        want = oracle.canonical(oracle.evaluate_bgp(G, b, is_set=True))
-        got = alone[key][0]
-        assert got[0] == want[0] and np.array_equal(got[1], want[1]), b
+    oracle_jobs.save_split_graph(oracle.split_by_predicate(G), str(tmp_path / "graph"))
+    del G
+    with oracle_pool(initializer=oracle_jobs.load_split_graph, initargs=(str(tmp_path / "graph"),)) as pool:
+        pending = pool.map_async(oracle_jobs.bgp_job, [bgps[i] for i in distinct])
+        with Context(device=0) as ctx:
+            ctx.load_triples(s, p, o)
+            ctx.serve_start(max_active=256, mem_budget_bytes=40 << 30)
+            tickets = []
+            for i in stream:
+                tickets.append(ctx.submit(bgps[i]))
+                time.sleep(0.0005)  # 2000 queries/s
+            served = [None] * len(stream)
+            deadline = time.time() + 300
+            while any(x is None for x in served) and time.time() < deadline:
+                for k, t in enumerate(tickets):
+                    if served[k] is None:
+                        res = ctx.poll(t)
+                        if res is not None:
+                            served[k] = oracle.canonical(host_rows(res))
+                            res.free()
+                time.sleep(0.001)
+            stats = ctx.serve_stats()
+            ctx.serve_stop()
+            assert all(x is not None for x in served)
+            assert stats["completed"] == len(stream) and stats["failed"] == 0
+            alone = {}
+            for i in distinct:
+                res = ctx.query(bgps[i])
+                alone[i] = oracle.canonical(host_rows(res))
+                res.free()
+        for k, i in enumerate(stream):
+            assert served[k][0] == alone[i][0] and np.array_equal(served[k][1], alone[i][1]), bgps[i]
+        wants = pending.get(timeout=1200)
+    assert sum(w[1].shape[0] for w in wants) > 0
+    for i, want in zip(distinct, wants):
+        got = alone[i]
+        assert got[0] == want[0] and np.array_equal(got[1], want[1]), bgps[i]
