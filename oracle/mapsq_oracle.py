@@ -23,6 +23,11 @@ What it computes (MapSQ, arXiv 1702.03484):
 * ``split_by_predicate``: the triple set grouped by predicate, so that a
   pattern with a constant predicate is filtered against that predicate's
   triples only (the same partial matches, a shorter linear filter).
+* ``project``: the SELECT clause of a query (Section 1, query Q selects
+  ?person): the solutions restricted to the selected variables, duplicates
+  kept (SPARQL's default bag semantics).
+* ``distinct``: SELECT DISTINCT, each distinct row once.
+* ``decode``: dictionary decoding of term ids back to their strings.
 * ``brute_force_bgp``: every assignment of the variables over the graph's terms,
   kept when each substituted pattern is a triple of the graph (the SPARQL
   definition of a BGP's solutions).
@@ -276,3 +281,24 @@ def brute_force_bgp(graph, bgp):
 def join_batch(pairs, join=join_mapreduce):
     """Independent joins, one after another."""
     return [join(L, R) for (L, R) in pairs]
+
+
+def project(t, vars_):
+    """SELECT ``vars_``: every solution restricted to those variables, in that
+    order; the number of rows is unchanged (no duplicate is removed)."""
+    tv, rows = as_rows(t)
+    cols = [tv.index(v) for v in vars_]
+    return list(vars_), np.ascontiguousarray(rows[:, cols]).reshape(rows.shape[0], len(cols))
+
+
+def distinct(t):
+    """SELECT DISTINCT: the table's distinct rows, each once (sorted)."""
+    tv, rows = as_rows(t)
+    if rows.shape[0] == 0 or rows.shape[1] == 0:
+        return tv, rows[: min(rows.shape[0], 1)]
+    return tv, np.unique(rows, axis=0)
+
+
+def decode(ids, terms):
+    """The string of each term id: ``terms[i]`` is the term with id i."""
+    return [terms[int(i)] for i in ids]

@@ -79,6 +79,45 @@ def test_table1_as_query():
     assert sorted(tuple(d.term(r[c]) for c in pos) for r in rows.tolist()) == expected
 
 
+def test_query_q_select_person():
+    """Query Q of Section 1 selects ?person: the answer is exactly Jim and Susan
+    (the golden [SELECT ?person] section), with or without DISTINCT, decoded
+    through the dictionary."""
+    graph, bgp, d, var_ids, header, expected = table1_query()
+    g = load()
+    want = sorted(r[0] for r in g["SELECT ?person"])
+    assert want == ["Jim", "Susan"]
+    sol = oracle.evaluate_bgp(graph, bgp)
+    for t in (oracle.project(sol, [var_ids["?person"]]), oracle.distinct(oracle.project(sol, [var_ids["?person"]]))):
+        vars_, rows = t
+        assert vars_ == [var_ids["?person"]]
+        assert sorted(oracle.decode(rows[:, 0], d.terms)) == want
+
+
+def test_project_and_distinct_match_brute_force():
+    """Projection keeps every solution (multiplicities counted independently with
+    Counter over brute-force assignments); DISTINCT keeps each projected row once
+    (a Python set); on tiny graphs, including projections that create duplicates."""
+    for seed in range(40):
+        graph = tiny_graph(seed + 500, n_terms=7, n_triples=30)
+        bgp = tiny_bgp(seed + 500, n_terms=7)
+        bv, brows = oracle.brute_force_bgp(graph, bgp)
+        if not bv:
+            continue
+        r = gen.Rng(seed, 21)
+        k = int(r.between(1, 1, len(bv))[0])
+        sel = [bv[int(i)] for i in r.permutation(len(bv))[:k]]
+        want = Counter(tuple(row[bv.index(v)] for v in sel) for row in brows.tolist())
+        pv, prow = oracle.project(oracle.evaluate_bgp(graph, bgp), sel)
+        assert pv == sel and Counter(map(tuple, prow.tolist())) == want, (seed, bgp, sel)
+        dv, drow = oracle.distinct((pv, prow))
+        assert dv == sel and sorted(map(tuple, drow.tolist())) == sorted(want), (seed, bgp, sel)
+    # a projection with duplicates: ?x has three ?y
+    rows = np.array([[1, 10], [1, 11], [1, 12], [2, 10]], np.uint32)
+    assert Counter(map(tuple, oracle.project(([0, 1], rows), [0])[1].tolist())) == Counter({(1,): 3, (2,): 1})
+    assert oracle.distinct(oracle.project(([0, 1], rows), [0]))[1].tolist() == [[1], [2]]
+
+
 # ---------------------------------------------------------------- pairwise join
 
 def key_histogram_count(L, R):
