@@ -860,12 +860,13 @@ def run_ours(args):
         launches0 = ctx.launch_count()
         barrier()
         torch.cuda.synchronize()
+        # clocks are sampled over the timed steps and the passes after them
         with ClockSampler(local) as clocks:
             total_ms, rows, step_ms = timed_steps(w, ctx, w.run_gpu, args.steps, flush, stream)
-        torch.cuda.synchronize()
-        barrier()
-        launches = ctx.launch_count() - launches0
-        head = measure_rest(ctx, w, args.steps, max(1, min(args.steps, 5)), flush, stream, peak, peak_kind)
+            torch.cuda.synchronize()
+            barrier()
+            launches = ctx.launch_count() - launches0
+            head = measure_rest(ctx, w, args.steps, max(1, min(args.steps, 5)), flush, stream, peak, peak_kind)
         extras = {}
         if args.workload == "skewed_join" and args.size == "full" and not args.no_extras and world == 1:
             w.release(ctx)

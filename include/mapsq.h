@@ -245,6 +245,27 @@ MAPSQ_API int mapsq_scan_pattern(mapsq_ctx* ctx, const mapsq_pattern* tp, mapsq_
 MAPSQ_API int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right, mapsq_table** out,
                const mapsq_join_opts* opts);
 
+/* A join whose result need not fit in device memory (the paper's GPU had
+ * 1536 MB, Section 3): Algorithm 1 on slices of the larger input, whose
+ * results together are the join, since every row of one slice finds all its
+ * matches in the other, whole input.  Each slice's result is computed on the
+ * device, copied to the caller's host columns (``host_cols[c]``, room for
+ * ``capacity_rows`` rows; columns in mapsq_join's order) after the slices
+ * before it, and freed; a slice whose count or result exceeds the context's
+ * memory budget or the device memory is halved and retried.  The smaller input
+ * is whole in every slice and must fit.  ``*out_rows`` receives the join's
+ * row count; ``host_cols`` NULL only counts; if the count exceeds
+ * capacity_rows the call returns MAPSQ_ERR_BUDGET after counting every slice
+ * (``*out_rows`` set, the host columns partly written).  On success ``*out``
+ * (may be NULL) describes the host result (on_device 0, columns =
+ * host_cols) and ``*slices`` (may be NULL) the number of slices.  Input
+ * columns must be on the device.  Synchronises at least once per slice.
+ * Errors: INVALID, UNSUPPORTED, BUDGET, OOM (a one-row slice does not fit),
+ * CUDA. */
+MAPSQ_API int mapsq_join_to_host(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right,
+                                 const mapsq_join_opts* opts, uint32_t* const* host_cols, uint64_t capacity_rows,
+                                 uint64_t* out_rows, mapsq_table* out, uint32_t* slices);
+
 /* Batched form: ``k`` independent joins (each as mapsq_join, Algorithm 1;
  * evaluating many at once has no counterpart in the paper) evaluated
  * together.  Every phase of the join (hash build, count, partition, write) is
@@ -334,6 +355,24 @@ MAPSQ_API void mapsq_table_free(mapsq_ctx* ctx, mapsq_table* t);
  * CUDA, TIMEOUT. */
 MAPSQ_API int mapsq_sync(mapsq_ctx* ctx);
 
+/* Bound every wait of a device thread on another (the look-back of the prefix
+ * scans) at ``spins`` polls of about 30-50 ns each (default 2^20, about 50
+ * ms); a wait that runs out sets
+ * the context's device status word and the kernel ends, and the next call
+ * that synchronises returns MAPSQ_ERR_TIMEOUT (the context stays usable).
+ * Infrastructure; the paper has no counterpart.  Errors: INVALID (spins == 0). */
+MAPSQ_API int mapsq_set_wait_limit(mapsq_ctx* ctx, uint32_t spins);
+
+/* Self-test of the bounded waits: runs a prefix scan of four tiles whose first
+ * tile no block ever takes, so each later tile's look-back waits for a
+ * predecessor that is never published; with the wait limit ``spins`` every
+ * such wait gives up, the kernel ends and the call returns MAPSQ_ERR_TIMEOUT
+ * (the expected result), after which the status word is clear and the context
+ * usable.  MAPSQ_OK would mean a wait did not give up.  Synchronises.
+ * Infrastructure; the paper has no counterpart.  Errors: INVALID, BUSY, OOM,
+ * BUDGET, CUDA; TIMEOUT as described. */
+MAPSQ_API int mapsq_selftest_wait(mapsq_ctx* ctx, uint32_t spins);
+
 /* Device memory currently held for tables and scratch, and its high-water mark. */
 MAPSQ_API int mapsq_memory_in_use(mapsq_ctx* ctx, uint64_t* bytes, uint64_t* peak_bytes);
 
@@ -355,6 +394,49 @@ MAPSQ_API int mapsq_reset_stats(mapsq_ctx* ctx);
 
 /* Number of CUDA kernels this context has launched since it was created. */
 MAPSQ_API int mapsq_launch_count(mapsq_ctx* ctx, uint64_t* launches);
+
+/* Flags of mapsq_project and mapsq_query_select. */
+#define MAPSQ_DISTINCT 1u
+
+/* The SELECT clause of a query (Section 1: query Q selects ?person from the
+ * solutions of its patterns): a new table holding the columns of ``t`` whose
+ * variables are ``vars[0 .. nvars)``, in that order.  Without MAPSQ_DISTINCT
+ * every row is kept (SPARQL's default bag semantics: one row per solution);
+ * with it each distinct row is kept once (SELECT DISTINCT; which of several
+ * equal rows survives is unspecified, their values being equal), in the
+ * order of the rows kept.  Columns of ``t`` must be on the device.  DISTINCT
+ * synchronises once (to size its result) and uses 12 bytes of scratch per row
+ * of ``t`` plus 4 per slot of its table (a power of two of at least twice the
+ * rows).  Errors: INVALID (NULL, nvars == 0, a variable not in ``t`` or given
+ * twice, unknown flags), UNSUPPORTED (DISTINCT over more than 2^31 rows), OOM,
+ * BUDGET, CUDA. */
+MAPSQ_API int mapsq_project(mapsq_ctx* ctx, const mapsq_table* t, uint32_t nvars, const int32_t* vars,
+                            uint32_t flags, mapsq_table** out);
+
+/* A BGP query with a SELECT clause: mapsq_query (Section 2) followed by
+ * mapsq_project of its solutions (Section 1, query Q); the full solution table
+ * is freed.  Errors: as mapsq_query and mapsq_project. */
+MAPSQ_API int mapsq_query_select(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, uint32_t nvars,
+                                 const int32_t* vars, uint32_t flags, mapsq_table** out);
+
+/* Load a term dictionary for mapsq_decode: term id i is the byte string
+ * ``bytes[offsets[i] .. offsets[i + 1])`` (host pointers; ``offsets`` has
+ * n_terms + 1 nondecreasing entries from 0; both are copied to the device).
+ * The dictionary is the inverse of the encoding that turned an RDF graph's
+ * terms into the uint32 ids of the triples (the paper's tables, Table 1, show
+ * terms as strings).  Replaces any previous dictionary.  Synchronises.
+ * Errors: INVALID, BUSY (serving), OOM, BUDGET, CUDA. */
+MAPSQ_API int mapsq_dict_load(mapsq_ctx* ctx, const uint64_t* offsets, const char* bytes, uint32_t n_terms);
+
+/* Decode column ``col`` of ``t`` (device columns) through the loaded
+ * dictionary: row r's string is written to ``bytes[offsets[r] .. offsets[r +
+ * 1])``.  ``offsets`` (host, caller-owned, t->nrows + 1 entries) is always
+ * filled and ``*nbytes`` receives offsets[t->nrows]; the bytes are written only
+ * when ``bytes`` is not NULL and *nbytes <= ``cap``, so a caller can size its
+ * buffer with a first call.  Synchronises.  Errors: INVALID (NULL, no
+ * dictionary, col out of range, an id with no term), OOM, BUDGET, CUDA. */
+MAPSQ_API int mapsq_decode(mapsq_ctx* ctx, const mapsq_table* t, uint32_t col, uint64_t* offsets, char* bytes,
+                           uint64_t cap, uint64_t* nbytes);
 
 /* Join two tables without allocating any memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc (a host that

@@ -12,7 +12,8 @@ const char* const kKernelNames[K_COUNT_KERNELS] = {
     "store_radix_histogram", "store_radix_scatter", "store_dedup", "store_predicate_heads",
     "scan_ranges",           "scan_emit",           "scan_filter", "prefix_sum",
     "hash_insert",           "hash_scatter",        "probe_count", "join_write",
-    "cross_write",           "copy",        "hll_sketch",  "write_partition", "sorted_count", "dense_write"};
+    "cross_write",           "copy",        "hll_sketch",  "write_partition", "sorted_count", "dense_write",
+    "partition_build"};
 
 int set_error(Ctx* ctx, int code, const char* fmt, ...) {
   if (ctx) {
@@ -208,6 +209,15 @@ int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count) {
   return check_status(ctx);
 }
 
+void dict_release(Ctx* ctx) {
+  if (ctx->dict_off) dev_free(ctx, ctx->dict_off, (uint64_t(ctx->dict_terms) + 1) * 8);
+  if (ctx->dict_bytes) dev_free(ctx, ctx->dict_bytes, std::max<uint64_t>(ctx->dict_nbytes, 1));
+  ctx->dict_off = nullptr;
+  ctx->dict_bytes = nullptr;
+  ctx->dict_terms = 0;
+  ctx->dict_nbytes = 0;
+}
+
 int check_status(Ctx* ctx) {
   // h_pinned[32] holds the status word read by the last synchronising call
   uint32_t st = uint32_t(ctx->h_pinned[32] & 0xFFFFFFFFu);
@@ -303,6 +313,7 @@ int mapsq_destroy(mapsq_ctx* ctx) {
   for (void* p : ctx->chunk_cache) dev_free(ctx, p, Scratch::kChunk);
   ctx->chunk_cache.clear();
   store_release(ctx);
+  dict_release(ctx);
   dev_free(ctx, ctx->d_status, 256);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -367,6 +378,16 @@ int mapsq_join(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right
   MQ_TRY(join_tables(ctx, left, right, opts, &t));
   *out = &t->pub;
   return MAPSQ_OK;
+}
+
+int mapsq_join_to_host(mapsq_ctx* ctx, const mapsq_table* left, const mapsq_table* right,
+                       const mapsq_join_opts* opts, uint32_t* const* host_cols, uint64_t capacity_rows,
+                       uint64_t* out_rows, mapsq_table* out, uint32_t* slices) {
+  if (!ctx || !left || !right || !out_rows)
+    return ctx ? set_error(ctx, MAPSQ_ERR_INVALID, "NULL argument") : MAPSQ_ERR_INVALID;
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  return join_to_host(ctx, left, right, opts, host_cols, capacity_rows, out_rows, out, slices);
 }
 
 int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* left, const mapsq_table* const* right,
@@ -451,6 +472,39 @@ int mapsq_sync(mapsq_ctx* ctx) {
   if (!ctx) return MAPSQ_ERR_INVALID;
   std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   MQ_CUDA(cudaSetDevice(ctx->device));
+  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
+}
+
+int mapsq_set_wait_limit(mapsq_ctx* ctx, uint32_t spins) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  if (spins == 0) return set_error(ctx, MAPSQ_ERR_INVALID, "a wait limit of 0 polls");
+  std::lock_guard<std::recursive_mutex> cl(ctx->mu);
+  ctx->wait_spins = spins;
+  return MAPSQ_OK;
+}
+
+int mapsq_selftest_wait(mapsq_ctx* ctx, uint32_t spins) {
+  if (!ctx) return MAPSQ_ERR_INVALID;
+  if (spins == 0) return set_error(ctx, MAPSQ_ERR_INVALID, "a wait limit of 0 polls");
+  if (ctx->server) return set_error(ctx, MAPSQ_ERR_BUSY, "the serving loop is running");
+  MQ_CUDA(cudaSetDevice(ctx->device));
+  constexpr uint64_t n = 4 * 4096;  // four look-back tiles
+  int rc = MAPSQ_OK;
+  {
+    Scratch scratch(ctx);
+    uint32_t* in = nullptr;
+    uint64_t* out = nullptr;
+    MQ_TRY(scratch.get(n, &in));
+    MQ_TRY(scratch.get(n + 1, &out));
+    MQ_CUDA(cudaMemsetAsync(in, 0, n * sizeof(uint32_t), ctx->stream));
+    const uint32_t saved = ctx->wait_spins;
+    ctx->wait_spins = spins;
+    rc = prefix_sum_withheld(ctx, in, out, n);
+    ctx->wait_spins = saved;
+  }
+  MQ_TRY(rc);
   MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
   MQ_CUDA(cudaStreamSynchronize(ctx->stream));
   return check_status(ctx);

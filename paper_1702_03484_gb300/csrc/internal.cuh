@@ -36,6 +36,7 @@ enum KernelId {
   K_PARTITION,
   K_SORTED_COUNT,
   K_DENSE_WRITE,
+  K_PARTITION_BUILD,
   K_COUNT_KERNELS
 };
 
@@ -123,6 +124,12 @@ struct mapsq_ctx {
   mapsq::KernelTotals totals[mapsq::K_COUNT_KERNELS];
   std::vector<mapsq::TableImpl*> live_tables;
   uint32_t sorted_ratio = 4;      // AUTO joins: sorted side rows / other side rows from which SORTED runs
+  uint32_t wait_spins = 1u << 20; // polls of a bounded device wait before it gives up (mapsq_set_wait_limit)
+  // term dictionary for mapsq_decode (device): id i is dict_bytes[dict_off[i] .. dict_off[i + 1])
+  uint64_t* dict_off = nullptr;
+  char* dict_bytes = nullptr;
+  uint32_t dict_terms = 0;
+  uint64_t dict_nbytes = 0;
   // scratch chunks kept for the next call (reused in stream order on ``stream``)
   static constexpr int kChunkCache = 4;
   std::vector<void*> chunk_cache;
@@ -219,6 +226,13 @@ int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes);
 // Read a few 64-bit words back from the device (synchronises the stream).
 int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count);
 
+// Frees the term dictionary (mapsq_dict_load, mapsq_destroy).
+void dict_release(Ctx* ctx);
+
+// SELECT (select.cu): columns of ``t`` holding ``vars``, DISTINCT with MAPSQ_DISTINCT.
+int project_table(Ctx* ctx, const mapsq_table* t, uint32_t nvars, const int32_t* vars, uint32_t flags,
+                  TableImpl** out);
+
 // Serving loop (serve.cu): stops and frees it (mapsq_destroy).
 void server_shutdown(Ctx* ctx);
 
@@ -229,6 +243,8 @@ int check_status(Ctx* ctx);
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
 int prefix_sum_u32_u64(Ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n);
 int prefix_sum_u32_u32(Ctx* ctx, const uint32_t* in, uint32_t* out, uint64_t n);
+// The same scan with its first tile withheld (every look-back wait runs out).
+int prefix_sum_withheld(Ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n);
 int copy_u32(Ctx* ctx, uint32_t* dst, const uint32_t* src, uint64_t n);
 
 // Store (store.cu).
@@ -256,6 +272,11 @@ int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const maps
                 TableImpl** out);
 int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
                const mapsq_join_opts* opts, TableImpl** out);
+
+// A join into caller host columns, slice by slice of its larger input (mapsq_join_to_host).
+int join_to_host(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
+                 uint32_t* const* host_cols, uint64_t capacity, uint64_t* out_rows, mapsq_table* out,
+                 uint32_t* slices);
 
 // Counts k joins, then writes, in order, those whose results fit together in
 // ``budget_bytes`` (0 = all): status[j] = 0 written (out[j] set), 1 deferred;

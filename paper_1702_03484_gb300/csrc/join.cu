@@ -64,7 +64,7 @@ constexpr int kHllRegs = 1 << kHllBits;
 constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides size the table by rows
 constexpr int kHllSpan = 16;                           // row tiles per sketch CTA (one flush per 32K rows)
 constexpr int kBucket = 4;
-constexpr int kPhases = 10;
+constexpr int kPhases = 11;
 constexpr int kDenseUnroll = 4;                        // probe rows of a thread unrolled in the dense write
 constexpr uint32_t kDenseMax = 16;                     // joins of at most this many matches per probe row: dense write
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
@@ -72,7 +72,15 @@ constexpr int kSortedThreads = 1024;                   // threads of the sorted 
 constexpr int kSortedItems = kRowTile / kSortedThreads;
 constexpr uint32_t kSortedRatio = 4;                   // default: sorted side at least this many times the other's rows
 
-enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS, PH_SORTED, PH_DENSE };
+constexpr int kRegionBits = 8;
+constexpr int kRegions = 1 << kRegionBits;             // build partitions, by the top bits of the home bucket
+constexpr int kHllWords = kHllRegs + kRegions;         // a sketch's registers, then its region histogram
+constexpr int kPartThreads = 512;                      // threads of the partition kernel
+constexpr int kPartItems = 16;
+constexpr int kPartRows = kPartThreads * kPartItems;   // build rows per partition CTA
+
+enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_WRITE, PH_CROSS, PH_SORTED, PH_DENSE,
+             PH_REGION };
 
 // Open-addressing table of the build side's distinct keys: ``keys`` holds M
 // 64-bit keys in buckets of 4 (one 32-byte sector), probed bucket after bucket
@@ -97,7 +105,7 @@ struct JoinDesc {
   KeyCols bk, pk;                 // build and probe keys
   uint64_t nb, np;                // build and probe rows
   HashTable t;
-  uint32_t* hll;                  // kHllRegs registers, or NULL
+  uint32_t* hll;                  // kHllRegs registers and kRegions region counts, or NULL
   uint32_t* slot_of;              // nb: slot of each build row
   uint32_t* rank_of;              // nb: rank inside its group
   uint64_t* slot_total;           // per slot tile: sum of its group sizes
@@ -150,10 +158,18 @@ __device__ __forceinline__ uint64_t mix_key(uint64_t k) {
 
 // Home bucket in [0, M / kBucket): Fibonacci (multiplicative) hashing of the
 // key, folded to 32 bits, then multiply-shift range reduction.
-__device__ __forceinline__ uint32_t home_bucket(uint64_t key, uint32_t M) {
+__device__ __forceinline__ uint32_t home_x(uint64_t key) {
   const uint32_t h = uint32_t((key * 0x9e3779b97f4a7c15ull) >> 32) ^ uint32_t(key >> 29);
-  return uint32_t((uint64_t(h * 0x85ebca6bu) * uint64_t(M / kBucket)) >> 32);
+  return h * 0x85ebca6bu;
 }
+
+__device__ __forceinline__ uint32_t home_bucket(uint64_t key, uint32_t M) {
+  return uint32_t((uint64_t(home_x(key)) * uint64_t(M / kBucket)) >> 32);
+}
+
+// Region of a key: the top bits of the same 32-bit value, so that the regions
+// cut the table into consecutive runs of home buckets whatever its size.
+__device__ __forceinline__ uint32_t home_region(uint64_t key) { return home_x(key) >> (32 - kRegionBits); }
 
 __device__ __forceinline__ uint64_t* bucket_keys(const HashTable& t, uint32_t b) {
   return t.keys + uint64_t(b) * kBucket;
@@ -233,28 +249,119 @@ __device__ __forceinline__ uint64_t block_scan(uint64_t sum, uint64_t* s_warp, u
 // HyperLogLog sketch of the build keys (Flajolet, Fusy, Gandouet, Meunier,
 // 2007): 2^12 registers hold the largest leading-zero count + 1 seen among the
 // hashes routed to them.  The input is salted so the hash is independent of the
-// table's.
+// table's.  The same pass counts the rows of each region (home_region), the
+// histogram of the build side's partition.
 __global__ void __launch_bounds__(kThreads) hll_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                       uint32_t k) {
   __shared__ uint32_t s[kHllRegs];
+  __shared__ uint32_t s_hist[kRegions];
   const uint32_t j = item_join(first, k, blockIdx.x);
   const JoinDesc& d = jd[j];
   const uint64_t base = (blockIdx.x - first[j]) * uint64_t(kRowTile) * kHllSpan;
   for (int r = threadIdx.x; r < kHllRegs; r += kThreads) s[r] = 0;
+  for (int r = threadIdx.x; r < kRegions; r += kThreads) s_hist[r] = 0;
   __syncthreads();
 #pragma unroll 8
   for (int it = 0; it < kRowItems * kHllSpan; ++it) {
     const uint64_t i = base + uint64_t(it) * kThreads + threadIdx.x;
     if (i < d.nb) {
-      const uint64_t h = mix_key(load_key(d.bk, i) ^ 0x9e3779b97f4a7c15ull);
+      const uint64_t key = load_key(d.bk, i);
+      const uint64_t h = mix_key(key ^ 0x9e3779b97f4a7c15ull);
       const uint64_t w = (h << kHllBits) | (1ull << (kHllBits - 1));
       const uint32_t reg = uint32_t(h >> (64 - kHllBits)), rho = uint32_t(__clzll(w) + 1);
       if (s[reg] < rho) atomicMax(&s[reg], rho);  // most rows cannot raise their register
+      atomicAdd(&s_hist[home_region(key)], 1u);
     }
   }
   __syncthreads();
   for (int r = threadIdx.x; r < kHllRegs; r += kThreads)
     if (s[r]) atomicMax(&d.hll[r], s[r]);
+  for (int r = threadIdx.x; r < kRegions; r += kThreads)
+    if (s_hist[r]) atomicAdd(&d.hll[kHllRegs + r], s_hist[r]);
+}
+
+// Partition of a large build side by region, so that the insert and the
+// scatter that follow touch the hash table and the grouped values one run of
+// consecutive slots at a time (L2-resident) instead of all over.  A CTA takes
+// kPartRows rows: it ranks every row inside its region (warp-aggregated
+// shared-memory counters), reserves each region's run in the output with one
+// atomic per region, then moves the rows column by column through shared
+// memory so that each region's rows leave as one contiguous run.
+struct PartDesc {
+  const uint32_t* src[MAPSQ_MAX_VARS];  // build columns: the key column(s), then the value columns
+  uint32_t* dst[MAPSQ_MAX_VARS];        // their partitioned copies
+  uint32_t* cursor;                     // kRegions: next free row of each region (starts at its offset)
+  uint64_t n;
+  int nkey, ncols;
+};
+
+__global__ void __launch_bounds__(kPartThreads, 2) partition_kernel(const PartDesc* __restrict__ pd, const uint64_t* first,
+                                                                uint32_t k) {
+  extern __shared__ __align__(16) uint32_t s_buf[];  // kPartRows values of one column, in region order
+  __shared__ uint8_t s_reg[kPartRows];               // region of each position of s_buf
+  __shared__ uint32_t s_cnt[kRegions], s_lo[kRegions], s_gb[kRegions], s_wsum[kRegions / 32];
+  const uint32_t j = item_join(first, k, blockIdx.x);
+  const PartDesc& p = pd[j];
+  const uint64_t base = (blockIdx.x - first[j]) * uint64_t(kPartRows);
+  const uint32_t n = uint32_t(min(uint64_t(kPartRows), p.n - base));
+  const unsigned lane = threadIdx.x & 31;
+  for (int r = threadIdx.x; r < kRegions; r += kPartThreads) s_cnt[r] = 0;
+  __syncthreads();
+  uint32_t pos[kPartItems];  // region << 24 | rank inside the region, then the row's position in s_buf
+#pragma unroll
+  for (int it = 0; it < kPartItems; ++it) {
+    const uint32_t i = uint32_t(it) * kPartThreads + threadIdx.x;
+    uint32_t reg = kRegions;  // past the end: no region
+    if (i < n) {
+      uint64_t key = __ldg(p.src[0] + base + i);
+      if (p.nkey == 2) key = (key << 32) | __ldg(p.src[1] + base + i);
+      reg = home_region(key);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, reg);
+    const int leader = __ffs(peers) - 1;
+    uint32_t rb = 0;
+    if (lane == unsigned(leader) && reg < kRegions) rb = atomicAdd(&s_cnt[reg], uint32_t(__popc(peers)));
+    rb = __shfl_sync(0xffffffffu, rb, leader);
+    pos[it] = reg < kRegions ? (reg << 24) | (rb + uint32_t(__popc(peers & ((1u << lane) - 1u)))) : ~0u;
+  }
+  __syncthreads();
+  // exclusive scan of the region counts, and each region's run in the output
+  uint32_t v = 0, inc = 0;
+  if (threadIdx.x < kRegions) {
+    v = inc = s_cnt[threadIdx.x];
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, inc, dd);
+      if (lane >= unsigned(dd)) inc += x;
+    }
+    if (lane == 31) s_wsum[threadIdx.x >> 5] = inc;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRegions) {
+    uint32_t before = 0;
+    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) before += s_wsum[w];
+    s_lo[threadIdx.x] = before + inc - v;
+    s_gb[threadIdx.x] = v ? atomicAdd(p.cursor + threadIdx.x, v) : 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kPartItems; ++it)
+    if (pos[it] != ~0u) {
+      const uint32_t reg = pos[it] >> 24;
+      pos[it] = s_lo[reg] + (pos[it] & 0xffffffu);
+      s_reg[pos[it]] = uint8_t(reg);
+    }
+  for (int c = 0; c < p.ncols; ++c) {
+#pragma unroll
+    for (int it = 0; it < kPartItems; ++it)
+      if (pos[it] != ~0u) s_buf[pos[it]] = __ldcs(p.src[c] + base + uint32_t(it) * kPartThreads + threadIdx.x);
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < n; q += kPartThreads) {
+      const uint32_t reg = s_reg[q];
+      __stcg(p.dst[c] + s_gb[reg] + (q - s_lo[reg]), s_buf[q]);
+    }
+    __syncthreads();
+  }
 }
 
 double hll_estimate(const uint32_t* regs) {
@@ -320,6 +427,40 @@ __global__ void __launch_bounds__(kThreads, 8) hash_insert_kernel(const JoinDesc
       d.slot_of[i] = s;
       d.rank_of[i] = base_rank + __popc(peers & ((1u << lane) - 1u));
     }
+  }
+}
+
+// The join's largest match count of a probe row (atomic maximum over warps).
+template <int N>
+__device__ __forceinline__ void join_max_count(const uint32_t (&v)[N], uint64_t* out) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int q = 0; q < N; ++q) m = max(m, v[q]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)m);
+}
+
+// A join whose probe side is one tile needs no tile scan: the count kernel
+// writes its tile offsets, its row count and, for a small output, its write
+// partition, searching the tile's offsets where the block still holds them in
+// shared memory (s_off[pad(i)] = output offset of probe row i).  The whole
+// block calls this after the offsets are in place.
+__device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t tile_sum, uint64_t* total,
+                                                   const uint32_t* s_off) {
+  if (threadIdx.x == 0) {
+    d.tile_base[0] = 0;
+    d.tile_base[1] = tile_sum;
+    *total = tile_sum;
+  }
+  const uint64_t ntw = (tile_sum + kWriteTile - 1) / kWriteTile;
+  if (tile_sum && ntw <= kEarlyTiles && threadIdx.x <= ntw) {
+    const uint32_t v = uint32_t(min(uint64_t(threadIdx.x) * kWriteTile, tile_sum - 1));
+    uint32_t lo = 0, hi = uint32_t(d.np);  // last probe row whose offset is <= v
+    while (lo < hi) {
+      const uint32_t m = (lo + hi) >> 1;
+      if (s_off[m + (m >> 5)] <= v) lo = m + 1; else hi = m;
+    }
+    d.part[threadIdx.x] = lo - 1;
   }
 }
 
@@ -463,39 +604,6 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
   }
 }
 
-// The join's largest match count of a probe row (atomic maximum over warps).
-template <int N>
-__device__ __forceinline__ void join_max_count(const uint32_t (&v)[N], uint64_t* out) {
-  uint32_t m = 0;
-#pragma unroll
-  for (int q = 0; q < N; ++q) m = max(m, v[q]);
-  m = __reduce_max_sync(0xffffffffu, m);
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)m);
-}
-
-// A join whose probe side is one tile needs no tile scan: the count kernel
-// writes its tile offsets, its row count and, for a small output, its write
-// partition, searching the tile's offsets where the block still holds them in
-// shared memory (s_off[pad(i)] = output offset of probe row i).  The whole
-// block calls this after the offsets are in place.
-__device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t tile_sum, uint64_t* total,
-                                                   const uint32_t* s_off) {
-  if (threadIdx.x == 0) {
-    d.tile_base[0] = 0;
-    d.tile_base[1] = tile_sum;
-    *total = tile_sum;
-  }
-  const uint64_t ntw = (tile_sum + kWriteTile - 1) / kWriteTile;
-  if (tile_sum && ntw <= kEarlyTiles && threadIdx.x <= ntw) {
-    const uint32_t v = uint32_t(min(uint64_t(threadIdx.x) * kWriteTile, tile_sum - 1));
-    uint32_t lo = 0, hi = uint32_t(d.np);  // last probe row whose offset is <= v
-    while (lo < hi) {
-      const uint32_t m = (lo + hi) >> 1;
-      if (s_off[m + (m >> 5)] <= v) lo = m + 1; else hi = m;
-    }
-    d.part[threadIdx.x] = lo - 1;
-  }
-}
 
 // Count phase, tile-local: every probe row's match count and group start
 // (kProbeIn lookups in flight per thread), the match bitmask, the exclusive
@@ -829,7 +937,11 @@ __device__ __forceinline__ void write_pair(const uint32_t* __restrict__ grouped,
   // row: two 16-byte loads per run
   bool u = true;
 #pragma unroll
-  for (int g = 0; g < kRuns; ++g) u &= idx[g * kVec + kVec - 1] == idx[g * kVec] + kVec - 1 && !(idx[g * kVec] & 1u);
+  for (int g = 0; g < kRuns; ++g) {
+    u &= !(idx[g * kVec] & 1u);
+#pragma unroll
+    for (int w = 1; w < kVec; ++w) u &= idx[g * kVec + w] == idx[g * kVec] + uint32_t(w);
+  }
   if (__all_sync(0xffffffffu, u)) {
 #pragma unroll
     for (int g = 0; g < kRuns; ++g) {
@@ -1127,6 +1239,8 @@ struct JoinPlan {
   uint64_t nb = 0, np = 0, T = 0, M = 0;
   bool cross = false, hash = false, hll = false, sorted = false;
   uint64_t maxc = 0;  // largest match count of a probe row (after the count phase)
+  bool part = false;  // the build side is partitioned by region before the insert (large hash builds)
+  std::vector<uint32_t> region_off;  // first row of each region in the partitioned build side
 };
 
 // A batch of k joins, split in two halves so that the caller can allocate the
@@ -1239,6 +1353,8 @@ struct BatchJoin {
   }
 
   // Distinct-key estimates of the large build sides, then the table sizes.
+  uint32_t pl_rows(uint32_t j) const { return uint32_t(plans[j].nb); }
+
   int size_tables() {
     std::vector<uint64_t> per(k, 0);
     uint32_t nh = 0;
@@ -1252,11 +1368,11 @@ struct BatchJoin {
     }
     if (nh) {
       uint32_t* regs = nullptr;
-      MQ_TRY(mem->get(size_t(nh) * kHllRegs, &regs));
-      MQ_TRY(cuda(cudaMemsetAsync(regs, 0, size_t(nh) * kHllRegs * 4, stream), "memset"));
+      MQ_TRY(mem->get(size_t(nh) * kHllWords, &regs));
+      MQ_TRY(cuda(cudaMemsetAsync(regs, 0, size_t(nh) * kHllWords * 4, stream), "memset"));
       uint32_t h = 0;
       for (uint32_t j = 0; j < k; ++j)
-        if (plans[j].hll) descs[j].hll = regs + size_t(h++) * kHllRegs;
+        if (plans[j].hll) descs[j].hll = regs + size_t(h++) * kHllWords;
       set_items(PH_HLL, per);
       MQ_TRY(upload_descs());
       int r = rec(K_HLL);
@@ -1266,13 +1382,22 @@ struct BatchJoin {
       for (auto& pl : plans) bytes += pl.hll ? 4.0 * pl.lay.nkey * pl.nb : 0;
       done(r, bytes);
       MQ_TRY(cuda(cudaGetLastError(), "hll_kernel"));
-      MQ_TRY(readback(regs, size_t(nh) * kHllRegs / 2));
+      MQ_TRY(readback(regs, size_t(nh) * kHllWords / 2));
       h = 0;
       for (uint32_t j = 0; j < k; ++j) {
         if (!plans[j].hll) continue;
-        const double est = hll_estimate(reinterpret_cast<const uint32_t*>(host.data()) + size_t(h++) * kHllRegs);
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(host.data()) + size_t(h++) * kHllWords;
+        const double est = hll_estimate(w);
         // load factor about 0.6
         plans[j].M = std::min<uint64_t>(plans[j].M, std::max<uint64_t>(1024, uint64_t(1.6 * est) + 1024));
+        // the partition's region offsets (exclusive prefix sums of the histogram)
+        plans[j].region_off.assign(kRegions, 0);
+        uint32_t run = 0;
+        for (int r = 0; r < kRegions; ++r) {
+          plans[j].region_off[r] = run;
+          run += w[kHllRegs + r];
+        }
+        plans[j].part = run == pl_rows(j);  // the histogram covers every row (it always should)
       }
     }
     for (auto& pl : plans) {
@@ -1285,7 +1410,7 @@ struct BatchJoin {
   // Descriptors, item offsets and a zeroed tail go up together, in one copy.
   // The tail holds the status word, the write phase's work counter, the joins'
   // row counts and their largest match counts per probe row, so that each
-  // upload resets the first two and one copy reads back all of them.
+  // upload resets them and one copy reads back all.
   uint64_t* d_tail = nullptr;
   size_t blob_bytes() const { return sizeof(JoinDesc) * k + sizeof(uint64_t) * first.size() + sizeof(uint64_t) * (2 + 2 * k); }
   int ensure_blob() {
@@ -1368,11 +1493,68 @@ struct BatchJoin {
     set_items(PH_SCATTER, scat);
     set_items(PH_COUNT, cnt);
     set_items(PH_SORTED, scnt);
+    return allocate_partition();
+  }
+
+  // Partitioned copies of the large build sides; the insert and the scatter
+  // then read the copies (the descriptors point at them).
+  std::vector<PartDesc> pdescs;
+  std::vector<uint32_t> pcursor;
+  unsigned char* d_pblob = nullptr;
+  int allocate_partition() {
+    std::vector<uint64_t> per(k, 0);
+    uint32_t npart = 0;
+    for (auto& pl : plans) npart += pl.hash && pl.part;
+    set_items(PH_REGION, per);
+    if (!npart) return MAPSQ_OK;
+    pdescs.assign(k, PartDesc{});
+    pcursor.assign(size_t(k) * kRegions, 0);
+    MQ_TRY(mem->get(sizeof(PartDesc) * k + 4 * pcursor.size(), &d_pblob));
+    uint32_t* d_cursor = reinterpret_cast<uint32_t*>(d_pblob + sizeof(PartDesc) * k);
+    for (uint32_t j = 0; j < k; ++j) {
+      const JoinPlan& pl = plans[j];
+      if (!pl.hash || !pl.part) continue;
+      JoinDesc& d = descs[j];
+      PartDesc& pd = pdescs[j];
+      pd.nkey = pl.lay.nkey;
+      pd.n = pl.nb;
+      pd.cursor = d_cursor + size_t(j) * kRegions;
+      for (int q = 0; q < pl.lay.nkey; ++q) pd.src[pd.ncols++] = pl.B->col[pl.bkey[q]];
+      for (int c = pl.lay.nkey; c < pl.lay.ncols; ++c)
+        if (pl.lay.side[c] == pl.bside) pd.src[pd.ncols++] = pl.B->col[pl.lay.col[c]];
+      uint32_t* copy = nullptr;
+      MQ_TRY(mem->get(size_t(pl.nb) * pd.ncols, &copy));
+      for (int c = 0; c < pd.ncols; ++c) pd.dst[c] = copy + size_t(pl.nb) * c;
+      d.bk = KeyCols{pd.dst[0], pl.lay.nkey == 2 ? pd.dst[1] : nullptr};
+      for (int v = 0; v < d.nbv; ++v) d.bsrc[v] = pd.dst[pl.lay.nkey + v];
+      std::copy(pl.region_off.begin(), pl.region_off.end(), pcursor.begin() + size_t(j) * kRegions);
+      per[j] = ceil_div(pl.nb, kPartRows);
+    }
+    set_items(PH_REGION, per);
     return MAPSQ_OK;
+  }
+
+  int partition_phase() {
+    if (!items(PH_REGION)) return MAPSQ_OK;
+    std::vector<unsigned char> blob(sizeof(PartDesc) * k + 4 * pcursor.size());
+    memcpy(blob.data(), pdescs.data(), sizeof(PartDesc) * k);
+    memcpy(blob.data() + sizeof(PartDesc) * k, pcursor.data(), 4 * pcursor.size());
+    MQ_TRY(upload(d_pblob, blob.data(), blob.size()));
+    double bytes = 0;
+    for (uint32_t j = 0; j < k; ++j) bytes += 8.0 * pdescs[j].ncols * pdescs[j].n;
+    const int smem = 4 * kPartRows;
+    MQ_TRY(set_smem_once(reinterpret_cast<const void*>(partition_kernel), 2, smem));
+    const int r = rec(K_PARTITION_BUILD);
+    partition_kernel<<<unsigned(items(PH_REGION)), kPartThreads, smem, stream>>>(
+        reinterpret_cast<const PartDesc*>(d_pblob), phase_first(PH_REGION), k);
+    launched();
+    done(r, bytes);
+    return cuda(cudaGetLastError(), "partition_kernel");
   }
 
   int count_phases() {
     MQ_TRY(upload_descs());
+    MQ_TRY(partition_phase());
     double bytes = 0;
     if (items(PH_INSERT)) {
       for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.nb : 0;
@@ -1438,13 +1620,19 @@ struct BatchJoin {
       if (attempt) mem->rewind(mark);
       MQ_TRY(allocate());
       MQ_TRY(count_phases());  // its upload zeroes the status word
-      // one copy: status word, work counter, row counts
+      // one copy: status word, work counter, row counts and largest counts
       host.assign(2 + 2 * size_t(k), 0);
       // through the context's pinned buffer when it is large enough (a pageable copy is slower)
-      uint64_t* dst = ctx && host.size() <= kPinnedWords ? ctx->h_pinned : host.data();
+      // (words 0-63 of it are left to read_u64 and the status word)
+      uint64_t* dst = ctx && host.size() + 64 <= kPinnedWords ? ctx->h_pinned + 64 : host.data();
       MQ_TRY(cuda(cudaMemcpyAsync(dst, d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
+      // the context's status word too: an earlier call's write phase may have set it
+      if (ctx)
+        MQ_TRY(cuda(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                    stream), "readback"));
       MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
       if (dst != host.data()) memcpy(host.data(), dst, host.size() * 8);
+      if (ctx) MQ_TRY(check_status(ctx));
       const uint32_t st = uint32_t(host[0]);
       if (st & 1u) {
         // a distinct-key estimate far too low: rebuild every table at two slots per build row
@@ -1463,6 +1651,19 @@ struct BatchJoin {
       }
       return MAPSQ_OK;
     }
+  }
+
+  // Raise a kernel's dynamic shared memory limit to ``bytes``, once per device
+  // (``which`` numbers the kernels that need it).
+  int set_smem_once(const void* fn, int which, int bytes) {
+    static std::atomic<uint64_t> done[3][4] = {};  // per kernel: a bit per device
+    int dev = 0;
+    MQ_TRY(cuda(cudaGetDevice(&dev), "cudaGetDevice"));
+    const uint64_t bit = uint64_t(1) << (dev & 63);
+    if (dev < 256 && (done[which][dev >> 6].load() & bit)) return MAPSQ_OK;
+    MQ_TRY(cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes), "cudaFuncSetAttribute"));
+    if (dev < 256) done[which][dev >> 6] |= bit;
+    return MAPSQ_OK;
   }
 
   // Partition and write phases into out[j] (ncols device columns of T rows each).
@@ -1523,15 +1724,7 @@ struct BatchJoin {
       }
       int r = rec(K_JOIN_WRITE);
       const unsigned grid = unsigned(std::min<uint64_t>(items(PH_WRITE), 152ull * 4));
-      static std::atomic<uint64_t> smem_set[4] = {};  // devices (bit per device) whose attribute is set
-      int dev = 0;
-      MQ_TRY(cuda(cudaGetDevice(&dev), "cudaGetDevice"));
-      const uint64_t bit = uint64_t(1) << (dev & 63);
-      if (dev >= 256 || !(smem_set[dev >> 6].load() & bit)) {
-        MQ_TRY(cuda(cudaFuncSetAttribute(join_write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWriteSmem),
-                    "cudaFuncSetAttribute"));
-        if (dev < 256) smem_set[dev >> 6] |= bit;
-      }
+      MQ_TRY(set_smem_once(reinterpret_cast<const void*>(join_write_kernel), 0, kWriteSmem));
       join_write_kernel<<<grid, kThreads, kWriteSmem, stream>>>(d_descs, phase_first(PH_WRITE), k, queue);
       launched();
       done(r, bytes);
@@ -1628,6 +1821,93 @@ int join_batch_admit(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const ma
 int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
                 TableImpl** out) {
   return join_batch(ctx, 1, &L, &R, opts, out);
+}
+
+// A join computed slice by slice of its larger input, each slice's result
+// copied to the caller's host columns and freed before the next (Algorithm 1
+// distributes over a split of one input: a row's matches all lie in the other,
+// whole input).  A slice whose count or result does not fit in the context's
+// memory (MAPSQ_ERR_BUDGET or MAPSQ_ERR_OOM) is halved and retried.
+int join_to_host(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,
+                 uint32_t* const* host_cols, uint64_t capacity, uint64_t* out_rows, mapsq_table* out,
+                 uint32_t* slices) {
+  if (opts && (opts->algorithm < MAPSQ_JOIN_AUTO || opts->algorithm > MAPSQ_JOIN_SORTED))
+    return set_error(ctx, MAPSQ_ERR_INVALID, "join algorithm %d", opts->algorithm);
+  Layout lay;
+  MQ_TRY(check_table(ctx, L, "left"));
+  MQ_TRY(check_table(ctx, R, "right"));
+  MQ_TRY(make_layout(ctx, L, R, &lay));
+  if (host_cols)
+    for (int c = 0; c < lay.ncols; ++c)
+      if (!host_cols[c]) return set_error(ctx, MAPSQ_ERR_INVALID, "host column %d is NULL", c);
+  const bool split_left = L->nrows >= R->nrows;
+  const mapsq_table* big = split_left ? L : R;
+  const uint64_t n = big->nrows;
+  uint64_t off = 0, chunk = std::max<uint64_t>(n, 1), total = 0;
+  uint32_t nslices = 0;
+  bool writing = host_cols != nullptr;  // false once the result is known to overflow the host columns
+  do {
+    const uint64_t c = std::min(chunk, n - off);
+    mapsq_table slice = *big;
+    slice.nrows = c;
+    for (uint32_t q = 0; q < slice.ncols; ++q)
+      if (slice.col[q]) slice.col[q] += off;
+    const mapsq_table* A = split_left ? &slice : L;
+    const mapsq_table* B = split_left ? R : &slice;
+    int rc;
+    uint64_t rows = 0;
+    {
+      Scratch scratch(ctx);
+      BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
+      bj.algorithm = opts ? opts->algorithm : MAPSQ_JOIN_AUTO;
+      bj.sorted_ratio = ctx->sorted_ratio;
+      rc = bj.prepare(1, &A, &B);
+      if (rc == MAPSQ_OK) rc = bj.count();
+      if (rc == MAPSQ_OK) rows = bj.plans[0].T;
+      if (rc == MAPSQ_OK && writing && total + rows > capacity) writing = false;
+      if (rc == MAPSQ_OK && writing && rows) {
+        TableImpl* t = nullptr;
+        rc = table_alloc(ctx, rows, uint32_t(lay.ncols), lay.var, &t);
+        if (rc == MAPSQ_OK) {
+          uint32_t* const* cols[1] = {t->pub.col};
+          rc = bj.write(cols);
+          for (int q = 0; q < lay.ncols && rc == MAPSQ_OK; ++q) {
+            const cudaError_t e = cudaMemcpyAsync(host_cols[q] + total, t->pub.col[q], rows * sizeof(uint32_t),
+                                                  cudaMemcpyDeviceToHost, ctx->stream);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaMemcpyAsync", __FILE__, __LINE__);
+          }
+          if (rc == MAPSQ_OK) {
+            const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cudaStreamSynchronize", __FILE__, __LINE__);
+          }
+          table_release(ctx, t);
+        }
+      }
+    }
+    if (rc == MAPSQ_ERR_BUDGET || rc == MAPSQ_ERR_OOM) {
+      if (c <= 1) return rc;  // a single row's join does not fit
+      chunk = c / 2;
+      continue;
+    }
+    MQ_TRY(rc);
+    total += rows;
+    off += c;
+    ++nslices;
+  } while (off < n);
+  *out_rows = total;
+  if (slices) *slices = nslices;
+  if (host_cols && total > capacity)
+    return set_error(ctx, MAPSQ_ERR_BUDGET, "the join has %llu rows, the host columns hold %llu",
+                     (unsigned long long)total, (unsigned long long)capacity);
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->nrows = host_cols ? total : 0;
+    out->ncols = uint32_t(lay.ncols);
+    for (int c = 0; c < MAPSQ_MAX_VARS; ++c) out->var[c] = c < lay.ncols ? lay.var[c] : -1;
+    for (int c = 0; c < lay.ncols && host_cols; ++c) out->col[c] = host_cols[c];
+    out->on_device = 0;
+  }
+  return MAPSQ_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -6,8 +6,9 @@
 // plus the total at index n, in one pass: every CTA takes the next tile by an
 // atomic ticket, publishes its tile's sum, then adds the sums of the tiles
 // before it as soon as they are published.  Waits on a predecessor are bounded:
-// after kLookbackSpinLimit polls the CTA records bit 2 in the status word and
-// goes on with the partial prefix it has, so a launch always ends.
+// after ``spin_limit`` polls (a launch parameter; kLookbackSpinDefault unless
+// the context sets another) the CTA records bit 2 in the status word and goes
+// on with the partial prefix it has, so a launch always ends.
 #pragma once
 
 #include <cstdint>
@@ -17,7 +18,7 @@ namespace mapsq {
 constexpr int kLbThreads = 256;
 constexpr int kLbItems = 16;
 constexpr int kLbTile = kLbThreads * kLbItems;
-constexpr uint32_t kLookbackSpinLimit = 1u << 24;
+constexpr uint32_t kLookbackSpinDefault = 1u << 20;  // about 50 ms of polls with 32 ns sleeps
 
 // status word of one tile: flag in the top two bits, sum in the low 62
 constexpr uint64_t kLbFlagAggregate = 1ull << 62;
@@ -32,7 +33,7 @@ __device__ __forceinline__ int lb_pad(int i) { return i + (i >> 4); }
 
 // Exclusive prefix of this tile (sum of all earlier tiles) by warp-wide look-back.
 __device__ __forceinline__ uint64_t lb_tile_prefix(uint64_t* tile_status, uint32_t tile, uint64_t aggregate,
-                                                   uint32_t* err) {
+                                                   uint32_t* err, uint32_t spin_limit) {
   const unsigned lane = threadIdx.x & 31;
   if (tile == 0) {
     if (lane == 0) atomicExch(reinterpret_cast<unsigned long long*>(&tile_status[0]), kLbFlagPrefix | aggregate);
@@ -51,7 +52,7 @@ __device__ __forceinline__ uint64_t lb_tile_prefix(uint64_t* tile_status, uint32
     // only the lanes up to that one are needed; wait while one of them is unpublished
     unsigned not_ready = __ballot_sync(0xffffffffu, (w >> 62) == 0) & ((2u << stop) - 1u);
     if (not_ready) {
-      if (++spins > kLookbackSpinLimit) {
+      if (++spins > spin_limit) {
         if (lane == 0) atomicOr(err, 2u);
         break;
       }
@@ -126,10 +127,10 @@ __device__ __forceinline__ uint64_t lb_block_scan(const uint64_t* s_val, uint64_
 
 // One tile of the scan over n values: ``sink`` receives every row's exclusive
 // prefix sum and the total.  ``scratch`` = [ticket, status[ntiles]], zeroed
-// before the launch.
+// before the launch; a ticket past the last tile does nothing.
 template <class Producer, class Sink>
 __device__ __forceinline__ void lookback_scan_tile(const Producer& prod, uint64_t n, const Sink& sink,
-                                                   uint64_t* scratch, uint32_t* err) {
+                                                   uint64_t* scratch, uint32_t* err, uint32_t spin_limit) {
   __shared__ uint64_t s_val[kLbTile + kLbTile / 16];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_warp[kLbThreads / 32];
@@ -139,12 +140,13 @@ __device__ __forceinline__ void lookback_scan_tile(const Producer& prod, uint64_
   __syncthreads();
   const uint32_t tile = s_tile;
   const uint64_t base = uint64_t(tile) * kLbTile;
+  if (base >= n) return;  // the same for the whole block
   prod.fill(base, n, s_val);
   __syncthreads();
   uint64_t excl;
   const uint64_t tile_sum = lb_block_scan(s_val, s_warp, &excl);
   if (warp == 0) {
-    uint64_t p = lb_tile_prefix(scratch + 1, tile, tile_sum, err);
+    uint64_t p = lb_tile_prefix(scratch + 1, tile, tile_sum, err, spin_limit);
     if (lane == 0) s_prefix = p;
   }
   __syncthreads();

@@ -9,10 +9,10 @@ namespace {
 template <class OutT>
 __global__ void __launch_bounds__(kLbThreads) prefix_sum_kernel(const uint32_t* __restrict__ in, uint64_t n,
                                                                 OutT* __restrict__ out, uint64_t* scratch,
-                                                                uint32_t* err) {
+                                                                uint32_t* err, uint32_t spin_limit) {
   LbArrayProducer v{in};
   LbArraySink<OutT> sink{out, n};
-  lookback_scan_tile(v, n, sink, scratch, err);
+  lookback_scan_tile(v, n, sink, scratch, err, spin_limit);
 }
 
 __global__ void copy_u32_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, uint64_t n) {
@@ -29,8 +29,11 @@ __global__ void copy_u32_kernel(uint32_t* __restrict__ dst, const uint32_t* __re
   }
 }
 
+// ``withhold_first``: the ticket counter starts at 1, so no CTA takes the
+// first tile and every other tile's look-back waits for a predecessor that is
+// never published (the bounded-wait self-test).
 template <class OutT>
-int prefix_sum_impl(Ctx* ctx, const uint32_t* in, OutT* out, uint64_t n) {
+int prefix_sum_impl(Ctx* ctx, const uint32_t* in, OutT* out, uint64_t n, bool withhold_first = false) {
   if (n == 0) {
     MQ_CUDA(cudaMemsetAsync(out, 0, sizeof(OutT), ctx->stream));
     return MAPSQ_OK;
@@ -41,8 +44,13 @@ int prefix_sum_impl(Ctx* ctx, const uint32_t* in, OutT* out, uint64_t n) {
   uint64_t* lb = nullptr;
   MQ_TRY(scratch.get(lookback_scratch_words(n), &lb));
   MQ_CUDA(cudaMemsetAsync(lb, 0, lookback_scratch_words(n) * sizeof(uint64_t), ctx->stream));
+  if (withhold_first) {
+    static const uint64_t one = 1;
+    MQ_CUDA(cudaMemcpyAsync(lb, &one, sizeof one, cudaMemcpyHostToDevice, ctx->stream));
+  }
   int rec = prof_begin(ctx, K_PREFIX_SUM);
-  prefix_sum_kernel<OutT><<<unsigned(ntiles), kLbThreads, 0, ctx->stream>>>(in, n, out, lb, ctx->d_status);
+  prefix_sum_kernel<OutT><<<unsigned(ntiles), kLbThreads, 0, ctx->stream>>>(in, n, out, lb, ctx->d_status,
+                                                                            ctx->wait_spins);
   ++ctx->launches;
   prof_end(ctx, rec, double(n) * (sizeof(uint32_t) + sizeof(OutT)));
   MQ_CUDA(cudaGetLastError());
@@ -57,6 +65,10 @@ int prefix_sum_u32_u64(Ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n) 
 
 int prefix_sum_u32_u32(Ctx* ctx, const uint32_t* in, uint32_t* out, uint64_t n) {
   return prefix_sum_impl<uint32_t>(ctx, in, out, n);
+}
+
+int prefix_sum_withheld(Ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t n) {
+  return prefix_sum_impl<uint64_t>(ctx, in, out, n, true);
 }
 
 int copy_u32(Ctx* ctx, uint32_t* dst, const uint32_t* src, uint64_t n) {

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmapsq.so")
 MAX_VARS = 16
 VAR_S, VAR_P, VAR_O = 1, 2, 4
 JOIN_AUTO, JOIN_HASH, JOIN_SORTED = 0, 1, 2
+DISTINCT = 1
 
 STATUS = {
     0: "OK", -1: "INVALID", -2: "UNSUPPORTED", -3: "OOM", -4: "BUDGET",
@@ -113,6 +114,16 @@ _SIGNATURES = {
     "mapsq_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(_TP)]),
     "mapsq_serve_stats": (C.c_int, [_P, C.POINTER(ServeCounters)]),
     "mapsq_serve_stop": (C.c_int, [_P]),
+    "mapsq_join_to_host": (C.c_int, [_P, _TP, _TP, C.POINTER(JoinOpts), C.POINTER(_P), C.c_uint64,
+                                     C.POINTER(C.c_uint64), _TP, C.POINTER(C.c_uint32)]),
+    "mapsq_set_wait_limit": (C.c_int, [_P, C.c_uint32]),
+    "mapsq_selftest_wait": (C.c_int, [_P, C.c_uint32]),
+    "mapsq_project": (C.c_int, [_P, _TP, C.c_uint32, C.POINTER(C.c_int32), C.c_uint32, C.POINTER(_TP)]),
+    "mapsq_query_select": (C.c_int, [_P, C.POINTER(Pattern), C.c_uint32, C.c_uint32, C.POINTER(C.c_int32),
+                                     C.c_uint32, C.POINTER(_TP)]),
+    "mapsq_dict_load": (C.c_int, [_P, C.POINTER(C.c_uint64), C.c_char_p, C.c_uint32]),
+    "mapsq_decode": (C.c_int, [_P, _TP, C.c_uint32, C.POINTER(C.c_uint64), _P, C.c_uint64,
+                               C.POINTER(C.c_uint64)]),
 }
 
 _lib = None
@@ -240,6 +251,75 @@ def mapsq_query(ctx, bgp):
     out = _TP()
     _check(ctx, lib().mapsq_query(ctx, arr, len(arr), C.byref(out)))
     return out
+
+
+def mapsq_join_to_host(ctx, left, right, capacity=None, opts=None):
+    """Join into host numpy columns slice by slice (see include/mapsq.h).
+    ``capacity=None`` counts first (a call with no host columns), then joins
+    into arrays of exactly that size.  Returns (vars, [uint32 columns], slices)."""
+    lp = left if isinstance(left, _TP) else C.pointer(left)
+    rp = right if isinstance(right, _TP) else C.pointer(right)
+    o = C.byref(opts) if opts else None
+    rows = C.c_uint64()
+    slices = C.c_uint32()
+    if capacity is None:
+        _check(ctx, lib().mapsq_join_to_host(ctx, lp, rp, o, None, 0, C.byref(rows), None, C.byref(slices)))
+        capacity = rows.value
+    ncols = len(set(lp.contents.var[: lp.contents.ncols]) | set(rp.contents.var[: rp.contents.ncols]))
+    cols = [np.zeros(max(int(capacity), 1), np.uint32) for _ in range(ncols)]
+    arr = (_P * max(ncols, 1))(*[c.ctypes.data for c in cols])
+    out = Table()
+    _check(ctx, lib().mapsq_join_to_host(ctx, lp, rp, o, arr, capacity, C.byref(rows), C.pointer(out),
+                                         C.byref(slices)))
+    n = rows.value
+    return list(out.var[: out.ncols]), [c[:n] for c in cols], slices.value
+
+
+def mapsq_set_wait_limit(ctx, spins):
+    _check(ctx, lib().mapsq_set_wait_limit(ctx, spins))
+
+
+def mapsq_selftest_wait(ctx, spins):
+    """Raises MapsqError TIMEOUT when the bounded waits give up as designed."""
+    _check(ctx, lib().mapsq_selftest_wait(ctx, spins))
+
+
+def mapsq_project(ctx, t, vars_, distinct=False):
+    arr = (C.c_int32 * max(len(vars_), 1))(*vars_)
+    out = _TP()
+    _check(ctx, lib().mapsq_project(ctx, t, len(vars_), arr, DISTINCT if distinct else 0, C.byref(out)))
+    return out
+
+
+def mapsq_query_select(ctx, bgp, vars_, distinct=False):
+    pats = pattern_array(bgp)
+    arr = (C.c_int32 * max(len(vars_), 1))(*vars_)
+    out = _TP()
+    _check(ctx, lib().mapsq_query_select(ctx, pats, len(pats), len(vars_), arr, DISTINCT if distinct else 0,
+                                         C.byref(out)))
+    return out
+
+
+def mapsq_dict_load(ctx, terms):
+    """``terms[i]``: the string of term id i (encoded as UTF-8)."""
+    enc = [t.encode() for t in terms]
+    offsets = np.zeros(len(enc) + 1, np.uint64)
+    offsets[1:] = np.cumsum([len(b) for b in enc], dtype=np.uint64)
+    blob = b"".join(enc)
+    _check(ctx, lib().mapsq_dict_load(ctx, offsets.ctypes.data_as(C.POINTER(C.c_uint64)), blob, len(enc)))
+
+
+def mapsq_decode(ctx, t, col):
+    """The strings of column ``col`` (a list of str, one per row)."""
+    n = int(t.contents.nrows)
+    offsets = np.zeros(n + 1, np.uint64)
+    total = C.c_uint64()
+    optr = offsets.ctypes.data_as(C.POINTER(C.c_uint64))
+    _check(ctx, lib().mapsq_decode(ctx, t, col, optr, None, 0, C.byref(total)))
+    buf = C.create_string_buffer(max(total.value, 1))
+    _check(ctx, lib().mapsq_decode(ctx, t, col, optr, C.cast(buf, _P), total.value, C.byref(total)))
+    raw = buf.raw[: total.value]
+    return [raw[int(offsets[r]):int(offsets[r + 1])].decode() for r in range(n)]
 
 
 def mapsq_table_from_columns(ctx, vars_, cols, nrows=None):
@@ -425,6 +505,10 @@ class TableRef:
         t = self.ptr.contents
         return [torch.as_tensor(_CudaArray(t.col[c], t.nrows), device="cuda") for c in range(t.ncols)]
 
+    def decode(self, col):
+        """The strings of column ``col`` through the context's dictionary."""
+        return mapsq_decode(self.ctx.handle, self.ptr, col)
+
     def free(self):
         if self.ptr:
             mapsq_table_free(self.ctx.handle, self.ptr)
@@ -477,8 +561,18 @@ class Context:
     def query_batch(self, bgps):
         return [TableRef(self, p) for p in mapsq_query_batch(self.handle, bgps)]
 
-    def query(self, bgp) -> TableRef:
-        return TableRef(self, mapsq_query(self.handle, bgp))
+    def query(self, bgp, select=None, distinct=False) -> TableRef:
+        """Solutions of a BGP; ``select``: the variables to keep (SELECT), with
+        ``distinct`` for SELECT DISTINCT."""
+        if select is None:
+            return TableRef(self, mapsq_query(self.handle, bgp))
+        return TableRef(self, mapsq_query_select(self.handle, bgp, list(select), distinct))
+
+    def project(self, t: TableRef, vars_, distinct=False) -> TableRef:
+        return TableRef(self, mapsq_project(self.handle, t.ptr, list(vars_), distinct))
+
+    def dict_load(self, terms):
+        mapsq_dict_load(self.handle, terms)
 
     def table(self, vars_, cols, nrows=None) -> TableRef:
         return TableRef(self, mapsq_table_from_columns(self.handle, list(vars_), list(cols), nrows))

@@ -17,20 +17,21 @@ import bench
 rank, world, local = bench.dist_env()
 dist.init_process_group("gloo")
 t_max, rows = bench.combine_ranks(10.0 + 5.0 * rank, 1000 * (rank + 1), world, "cpu")
-print(json.dumps({{"rank": rank, "t_max": t_max, "rows": rows}}), flush=True)
+with open(os.path.join({out!r}, f"rank{{rank}}.json"), "w") as f:  # one file per rank: no interleaved lines
+    json.dump({{"rank": rank, "t_max": t_max, "rows": rows}}, f)
 dist.destroy_process_group()
 """
 
 
 def test_two_gloo_ranks_combine_max_time_and_summed_rows(tmp_path):
     script = tmp_path / "worker.py"
-    script.write_text(WORKER.format(root=ROOT))
+    script.write_text(WORKER.format(root=ROOT, out=str(tmp_path)))
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
            "--master-addr=127.0.0.1", "--master-port=29561", str(script)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=240, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     import json
-    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    lines = [json.loads((tmp_path / f"rank{i}.json").read_text()) for i in range(2)]
     assert sorted(x["rank"] for x in lines) == [0, 1]
     for x in lines:
         assert x["t_max"] == 15.0 and x["rows"] == 3000.0

@@ -85,6 +85,37 @@ def test_hot_key_on_build_side(ctx):
     assert n >= 40 * 3000
 
 
+def test_large_build_sides(ctx):
+    """Build sides of 2^16 rows and more take the region-partitioned build and,
+    when no key group exceeds sixteen rows, the fused write: ragged sizes, many
+    value columns, one- and two-variable keys, a hot build key (one region far
+    larger than the others, and the partitioned write) and all build rows in
+    one key."""
+    r = gen.Rng(15)
+    n = 70_001
+    # many value columns, key groups of at most a few rows: partitioned build, fused write
+    B = gen.Table([0, 1, 2, 3, 4, 5], [r.below(n, 40_000).astype(np.uint32)] + [r.u32(n) for _ in range(5)])
+    P = gen.Table([0, 9], [r.below(150_003, 40_000).astype(np.uint32), r.u32(150_003)])
+    join_and_check(ctx, P, B, "five build value columns")
+    # two-variable key, probe side of one partial tile
+    x, y = r.below(n, 300).astype(np.uint32), r.below(n, 300).astype(np.uint32)
+    B2 = gen.Table([0, 1, 6], [x, y, r.u32(n)])
+    P2 = gen.Table([7, 1, 0], [r.u32(90_017), r.below(90_017, 300).astype(np.uint32),
+                               r.below(90_017, 300).astype(np.uint32)])
+    join_and_check(ctx, B2, P2, "two-variable key")
+    # a hot key with 40% of the build rows
+    hk = r.below(n, 60_000).astype(np.uint32)
+    hk[r.below(28_000, n)] = 12345
+    B3 = gen.Table([0, 2], [hk, r.u32(n)])
+    P3 = gen.Table([0, 1], [np.concatenate((np.full(30, 12345, np.uint32), r.below(100_000, 60_000).astype(np.uint32))),
+                            r.u32(100_030)])
+    assert join_and_check(ctx, P3, B3, "hot build key") >= 30 * 20_000
+    # every build row in one key
+    B4 = gen.Table([0, 2], [np.full(1 << 16, 77, np.uint32), r.u32(1 << 16)])
+    P4 = gen.Table([0, 1], [np.array([77, 1, 77], np.uint32), r.u32(3)])
+    assert join_and_check(ctx, P4, B4, "one key") == 2 << 16
+
+
 def test_build_side_either_way(ctx):
     r = gen.Rng(6)
     small = gen.Table([0, 1, 3], [r.below(100, 64).astype(np.uint32), r.u32(100), r.u32(100)])
@@ -185,16 +216,16 @@ def test_profiling_reports_kernels(ctx):
     join_and_check(ctx, L, R, "profiled")
     stats = ctx.kernel_stats()
     ctx.set_profiling(False)
-    write = "join_write" if "join_write" in stats else "dense_write"
+    write = next(w for w in ("join_write", "dense_write") if w in stats)
     for k in ("hash_insert", "hash_scatter", "probe_count", "prefix_sum", write):
         assert stats[k]["launches"] >= 1 and stats[k]["device_ms"] > 0
     assert stats[write]["alg_bytes"] > 12 * 30000
 
 
 def test_dense_write_path(ctx):
-    """Joins of at most four matches per probe row take the dense write: rows of
-    exactly four aligned matches (16-byte stores) and of 0-3 matches (single
-    stores), hash and sorted sides, against the oracle."""
+    """Joins of at most sixteen matches per probe row take the dense write (a
+    thread per probe row): rows of exactly four aligned matches (16-byte
+    stores) and of 0-3 matches (single stores), against the oracle."""
     ctx.reset_stats()
     ctx.set_profiling(True)
     try:
@@ -331,3 +362,63 @@ def test_to_host_into_caller_arrays(ctx):
     with pytest.raises(ValueError):
         out.to_host([np.zeros(3, np.uint32)] * len(out.vars))
     out.free()
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(ctx):
+    """A prefix scan whose first tile is never taken: every look-back waits for
+    a predecessor that is never published, gives up after the wait limit, and
+    the call returns TIMEOUT; afterwards the status word is clear and joins
+    are exact again."""
+    from paper_1702_03484_gb300 import mapsq
+    from paper_1702_03484_gb300.mapsq import MapsqError
+    for spins in (1, 1000):
+        with pytest.raises(MapsqError) as e:
+            mapsq.mapsq_selftest_wait(ctx.handle, spins)
+        assert e.value.name == "TIMEOUT"
+        ctx.sync()  # the status word was cleared when the timeout was reported
+        L, R = gen.pairwise_uniform(seed=1, n_left=3000, n_right=2000, key_domain=500)
+        join_and_check(ctx, L, R, "after a timeout")
+    mapsq.mapsq_set_wait_limit(ctx.handle, 1 << 20)
+
+
+def test_join_to_host_in_slices_under_a_small_budget():
+    """A join whose result is several times the context's memory budget is
+    computed slice by slice into host columns and equals the oracle; a count
+    without host columns gives the same row count; too small host columns give
+    BUDGET with the row count."""
+    import ctypes as C
+    import torch
+    from paper_1702_03484_gb300 import Context, mapsq
+    from paper_1702_03484_gb300.mapsq import MapsqError
+    r = gen.Rng(17)
+    nl, nr = 1 << 18, 1 << 13
+    L = gen.Table([0, 1, 2], [r.below(nl, 1 << 11).astype(np.uint32), r.u32(nl), r.u32(nl)])
+    R = gen.Table([3, 0], [r.u32(nr), r.below(nr, 1 << 11).astype(np.uint32)])
+    want = oracle.join_mapreduce(L, R)
+    out_bytes = want[1].nbytes
+    lc = [torch.from_numpy(c).cuda() for c in L.cols]
+    rc = [torch.from_numpy(c).cuda() for c in R.cols]
+    lv, rv = mapsq.table_view(L.vars, lc), mapsq.table_view(R.vars, rc)
+    with Context(device=0, budget=out_bytes // 6) as small:
+        with pytest.raises(MapsqError) as e:
+            mapsq.mapsq_join(small.handle, C.pointer(lv), C.pointer(rv))
+        assert e.value.name == "BUDGET"  # the plain join does not fit
+        vars_, cols, slices = mapsq.mapsq_join_to_host(small.handle, lv, rv)
+        assert slices >= 6
+        class Host:
+            nrows = cols[0].shape[0]
+            @staticmethod
+            def to_host():
+                return vars_, cols
+        assert_same_multiset(Host, want, "sliced join")
+        with pytest.raises(MapsqError) as e:
+            mapsq.mapsq_join_to_host(small.handle, lv, rv, capacity=want[1].shape[0] - 1)
+        assert e.value.name == "BUDGET"
+        # the right side as the larger one, sliced the other way
+        vars2, cols2, _ = mapsq.mapsq_join_to_host(small.handle, rv, lv)
+        class Host2:
+            nrows = cols2[0].shape[0]
+            @staticmethod
+            def to_host():
+                return vars2, cols2
+        assert_same_multiset(Host2, oracle.join_mapreduce(R, L), "sliced join, larger side right")
