@@ -8,5 +8,5 @@ from .mapsq_oracle import (  # noqa: F401
     LEFT, RIGHT, VAR_S, VAR_P, VAR_O,
     as_rows, canonical, join_nested_loop, join_mapreduce, distinct_triples,
     scan_pattern, evaluate_bgp, brute_force_bgp, join_batch, split_by_predicate,
-    project, distinct, decode,
+    project, distinct, decode, join_star,
 )

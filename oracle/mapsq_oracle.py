@@ -23,6 +23,10 @@ What it computes (MapSQ, arXiv 1702.03484):
 * ``split_by_predicate``: the triple set grouped by predicate, so that a
   pattern with a constant predicate is filtered against that predicate's
   triples only (the same partial matches, a shorter linear filter).
+* ``join_star``: the join of k tables that share one variable and no other
+  (a star of patterns around it), in one step: for every value of that
+  variable, every combination of one row from each table holding it -- the
+  key/value framing of Section 1 and Algorithm 1 with k inputs instead of two.
 * ``project``: the SELECT clause of a query (Section 1, query Q selects
   ?person): the solutions restricted to the selected variables, duplicates
   kept (SPARQL's default bag semantics).
@@ -302,3 +306,28 @@ def distinct(t):
 def decode(ids, terms):
     """The string of each term id: ``terms[i]`` is the term with id i."""
     return [terms[int(i)] for i in ids]
+
+
+def join_star(tables, key_var):
+    """k tables (each with the column ``key_var``; no other variable in two of
+    them): for every key value x, every combination (x, rest of a row of table
+    1 with key x, ..., rest of a row of table k with key x).  Columns: the key,
+    then each table's other columns in table order.  Plain nested products per
+    key (small inputs)."""
+    tabs = [as_rows(t) for t in tables]
+    rest = [[c for c, v in enumerate(tv) if v != key_var] for tv, _ in tabs]
+    others = [v for (tv, _), rc in zip(tabs, rest) for v in (tv[c] for c in rc)]
+    assert len(others) == len(set(others)) and key_var not in others, "tables share more than the key"
+    out_vars = [key_var] + others
+    groups = []
+    for (tv, rows), rc in zip(tabs, rest):
+        kc = tv.index(key_var)
+        g = {}
+        for r in rows.tolist():
+            g.setdefault(r[kc], []).append([r[c] for c in rc])
+        groups.append(g)
+    out = []
+    for x in sorted(set.intersection(*[set(g) for g in groups])) if groups else []:
+        for combo in itertools.product(*[g[x] for g in groups]):
+            out.append([x] + [v for part in combo for v in part])
+    return out_vars, np.asarray(out, dtype=np.uint32).reshape(len(out), len(out_vars))

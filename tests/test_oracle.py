@@ -118,6 +118,61 @@ def test_project_and_distinct_match_brute_force():
     assert oracle.distinct(oracle.project(([0, 1], rows), [0]))[1].tolist() == [[1], [2]]
 
 
+def star_tables(seed, k, n_max=30, dom=6):
+    """k random tables sharing variable 0 and nothing else."""
+    r = gen.Rng(seed, 31)
+    tabs, nxt = [], 1
+    for _ in range(k):
+        extra = int(r.between(1, 0, 2)[0])
+        vars_ = [0] + list(range(nxt, nxt + extra))
+        nxt += extra
+        perm = r.permutation(len(vars_))
+        vars_ = [vars_[i] for i in perm]
+        tabs.append(gen.random_table(r, int(r.between(1, 0, n_max)[0]), vars_, dom))
+    return tabs
+
+
+def test_star_join_matches_pairwise_joins_and_histograms():
+    """The k-way star join equals k - 1 pairwise joins (Algorithm 1) in order,
+    and its row count is the sum over keys of the product of the tables' key
+    counts, from independent Counter histograms."""
+    for seed in range(60):
+        k = 2 + seed % 5
+        tabs = star_tables(seed, k)
+        got = oracle.join_star(tabs, 0)
+        acc = tabs[0]
+        for t in tabs[1:]:
+            acc = oracle.join_nested_loop(acc, t)
+        assert multiset(got) == multiset(acc), seed
+        hist = [Counter(t.cols[t.vars.index(0)].tolist()) for t in tabs]
+        keys = set(hist[0]).intersection(*hist[1:])
+        assert got[1].shape[0] == sum(int(np.prod([h[x] for h in hist])) for x in keys)
+
+
+def test_star_bgp_equals_brute_force():
+    """A star BGP (every pattern on one centre variable, no other variable
+    shared) evaluated by one star join of its partial matches equals brute
+    force."""
+    done = 0
+    for seed in range(200):
+        graph = tiny_graph(seed + 900, n_terms=6, n_triples=30, n_pred=3)
+        r = gen.Rng(seed, 41)
+        k = int(r.between(1, 2, 4)[0])
+        bgp, nxt = [], 1
+        for _ in range(k):
+            if r.below(1, 2)[0]:
+                bgp.append((0, int(r.below(1, 3)[0]), nxt, 5)); nxt += 1   # ?x p ?y
+            else:
+                bgp.append((nxt, int(r.below(1, 3)[0]), 0, 5)); nxt += 1   # ?y p ?x
+        g = oracle.distinct_triples(*graph)
+        parts = [oracle.scan_pattern(g, pat) for pat in bgp]
+        got = oracle.join_star(parts, 0)
+        want = oracle.brute_force_bgp(graph, bgp)
+        assert multiset(got) == multiset(want), (seed, bgp)
+        done += got[1].shape[0] > 0
+    assert done > 20
+
+
 # ---------------------------------------------------------------- pairwise join
 
 def key_histogram_count(L, R):
