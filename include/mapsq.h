@@ -266,6 +266,21 @@ MAPSQ_API int mapsq_join_to_host(mapsq_ctx* ctx, const mapsq_table* left, const 
                                  const mapsq_join_opts* opts, uint32_t* const* host_cols, uint64_t capacity_rows,
                                  uint64_t* out_rows, mapsq_table* out, uint32_t* slices);
 
+/* Multi-way join of ``k`` (2 to 8) tables that share exactly one variable,
+ * ``key_var`` (the partial matches of a star of triple patterns around it):
+ * the key/value framing of Section 1 and Algorithm 1 with k inputs instead of
+ * two, in one count and write round instead of k - 1 pairwise joins.  Result:
+ * for every key value, every combination of one row from each table holding
+ * it; columns: the key, then each table's other columns in table order (the
+ * order k - 1 pairwise joins give).  Every table but one must be sorted on
+ * the key (sorted_mask; scan results sorted on it are); otherwise the tables
+ * are joined pairwise, with the same result.  Synchronises once.  Errors:
+ * INVALID (NULL, k out of range, a table without the key, a variable other
+ * than the key in two tables, more than 16 result columns), UNSUPPORTED (one
+ * key's product beyond 2^32 rows), OOM, BUDGET, CUDA. */
+MAPSQ_API int mapsq_join_star(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* tables, int32_t key_var,
+                              mapsq_table** out);
+
 /* Batched form: ``k`` independent joins (each as mapsq_join, Algorithm 1;
  * evaluating many at once has no counterpart in the paper) evaluated
  * together.  Every phase of the join (hash build, count, partition, write) is
@@ -280,8 +295,10 @@ MAPSQ_API int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* co
 /* Evaluate a BGP of ``n`` patterns (Section 2: match each pattern, join the
  * partial results after each match).  The host orders the patterns: the one
  * with fewest matches first, then repeatedly the one with fewest matches among
- * those sharing a variable with the joined ones.  Result columns are the BGP's
- * variables in ascending id.  Errors: as mapsq_scan_pattern and mapsq_join. */
+ * those sharing a variable with the joined ones.  A star of 3 to 8 patterns
+ * (one variable in every pattern, no other variable in two) is joined in one
+ * round instead (mapsq_join_star).  Result columns are the BGP's variables in
+ * ascending id.  Errors: as mapsq_scan_pattern and mapsq_join. */
 MAPSQ_API int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, mapsq_table** out);
 
 /* Batched form of mapsq_query: ``nq`` BGPs (bgps[q] with n[q] patterns, each

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmapsq.so")
 
-SOURCES = ["api.cu", "prim.cu", "store.cu", "scan.cu", "join.cu", "query.cu", "serve.cu", "autotune.cu", "select.cu"]
+SOURCES = ["api.cu", "prim.cu", "store.cu", "scan.cu", "join.cu", "query.cu", "serve.cu", "autotune.cu", "select.cu", "star.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

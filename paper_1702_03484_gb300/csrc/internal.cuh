@@ -37,6 +37,8 @@ enum KernelId {
   K_SORTED_COUNT,
   K_DENSE_WRITE,
   K_PARTITION_BUILD,
+  K_STAR_COUNT,
+  K_STAR_WRITE,
   K_COUNT_KERNELS
 };
 
@@ -272,6 +274,9 @@ int join_tables(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const maps
                 TableImpl** out);
 int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_table* const* R,
                const mapsq_join_opts* opts, TableImpl** out);
+
+// Star join (star.cu): k tables sharing only ``key_var``, in one count and write round.
+int join_star(Ctx* ctx, uint32_t k, const mapsq_table* const* tabs, int32_t key_var, TableImpl** out);
 
 // A join into caller host columns, slice by slice of its larger input (mapsq_join_to_host).
 int join_to_host(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const mapsq_join_opts* opts,

@@ -24,6 +24,22 @@ uint32_t pattern_var_set(const mapsq_pattern& tp) {
 
 }  // namespace
 
+// The centre of a star BGP of 3 to 8 patterns: the one variable that every
+// pattern holds, with no other variable in two patterns; -1 otherwise.
+int32_t star_centre(const mapsq_pattern* bgp, uint32_t n) {
+  if (n < 3 || n > 8) return -1;
+  uint32_t common = ~0u, all = 0, twice = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t m = pattern_var_set(bgp[i]);
+    if (!m) return -1;
+    common &= m;
+    twice |= all & m;
+    all |= m;
+  }
+  if (__builtin_popcount(common) != 1 || twice != common) return -1;
+  return __builtin_ctz(common);
+}
+
 // Permute the columns of a result so that its variables are in ascending id
 // (a pointer permutation: no data moves; the sorted-column bits follow).
 void canonical_columns(mapsq_table* t) {
@@ -87,6 +103,26 @@ int query_batch(Ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const u
   if (!ctx->store.loaded) return set_error(ctx, MAPSQ_ERR_INVALID, "no triple store loaded");
   std::vector<PatternRange> ranges(all.size());
   MQ_TRY(scan_ranges(ctx, all.data(), uint32_t(all.size()), ranges.data()));
+
+  // one query that is a star: its patterns' matches, each sorted on the
+  // centre, joined in one round
+  const int32_t centre = nq == 1 ? star_centre(bgps[0], ns[0]) : -1;
+  if (centre >= 0) {
+    std::vector<TableImpl*> parts(ns[0], nullptr);
+    int rc = MAPSQ_OK;
+    for (uint32_t i = 0; i < ns[0] && rc == MAPSQ_OK; ++i) rc = scan_emit(ctx, bgps[0][i], ranges[i], &parts[i], centre);
+    TableImpl* res = nullptr;
+    if (rc == MAPSQ_OK) {
+      std::vector<const mapsq_table*> tabs;
+      for (auto* p : parts) tabs.push_back(&p->pub);
+      rc = join_star(ctx, ns[0], tabs.data(), centre, &res);
+    }
+    for (auto* p : parts) table_release(ctx, p);
+    if (rc != MAPSQ_OK) return rc;
+    canonical_columns(&res->pub);
+    out[0] = res;
+    return MAPSQ_OK;
+  }
 
   std::vector<std::vector<uint32_t>> order(nq);
   std::vector<TableImpl*> acc(nq, nullptr);

@@ -116,6 +116,7 @@ _SIGNATURES = {
     "mapsq_serve_stop": (C.c_int, [_P]),
     "mapsq_join_to_host": (C.c_int, [_P, _TP, _TP, C.POINTER(JoinOpts), C.POINTER(_P), C.c_uint64,
                                      C.POINTER(C.c_uint64), _TP, C.POINTER(C.c_uint32)]),
+    "mapsq_join_star": (C.c_int, [_P, C.c_uint32, C.POINTER(_TP), C.c_int32, C.POINTER(_TP)]),
     "mapsq_set_wait_limit": (C.c_int, [_P, C.c_uint32]),
     "mapsq_selftest_wait": (C.c_int, [_P, C.c_uint32]),
     "mapsq_project": (C.c_int, [_P, _TP, C.c_uint32, C.POINTER(C.c_int32), C.c_uint32, C.POINTER(_TP)]),
@@ -273,6 +274,13 @@ def mapsq_join_to_host(ctx, left, right, capacity=None, opts=None):
                                          C.byref(slices)))
     n = rows.value
     return list(out.var[: out.ncols]), [c[:n] for c in cols], slices.value
+
+
+def mapsq_join_star(ctx, tables, key_var):
+    arr = (_TP * len(tables))(*[t if isinstance(t, _TP) else C.pointer(t) for t in tables])
+    out = _TP()
+    _check(ctx, lib().mapsq_join_star(ctx, len(tables), arr, key_var, C.byref(out)))
+    return out
 
 
 def mapsq_set_wait_limit(ctx, spins):
@@ -553,6 +561,9 @@ class Context:
 
     def join(self, left: TableRef, right: TableRef, opts=None) -> TableRef:
         return TableRef(self, mapsq_join(self.handle, left.ptr, right.ptr, opts))
+
+    def join_star(self, tables, key_var) -> TableRef:
+        return TableRef(self, mapsq_join_star(self.handle, [t.ptr for t in tables], key_var))
 
     def join_batch(self, lefts, rights, opts=None):
         return [TableRef(self, p) for p in mapsq_join_batch(self.handle, [x.ptr for x in lefts],
