@@ -551,6 +551,20 @@ def oracle_all_cores(args, budget_s=10.0):
     return rows / max(dt for _, _, dt in res), cores, units
 
 
+def autotune_summary(tune):
+    """The autotuner's choices and the times they come from (ms, best of three)."""
+    if tune.get("fixed"):
+        return tune
+    return {"sorted_ratio": tune["sorted_ratio"],
+            "points": [(p["ratio"], round(p["hash_ms"], 3), round(p["sorted_ms"], 3)) for p in tune["points"]],
+            "partitioned_build_from_rows": tune["part_min_build"],
+            "size_points": [(p["build_rows"], round(p["partitioned_ms"], 3), round(p["plain_ms"], 3))
+                            for p in tune["size_points"]],
+            "dense_write_up_to_matches": tune["dense_max"],
+            "skew_points": [(p["group_rows"], round(p["dense_ms"], 3), round(p["partitioned_write_ms"], 3))
+                            for p in tune["skew_points"]]}
+
+
 def tuned(ctx, args):
     """The hash-vs-sorted crossover for this GPU: measured (not timed), or fixed."""
     if args.sorted_ratio:
@@ -903,9 +917,7 @@ def run_ours(args):
     line.update({
         "store_build": ({"seconds": w.store_build_s, "triples_per_s": len(w.s) / w.store_build_s}
                         if hasattr(w, "store_build_s") else None),
-        "autotune": {"sorted_ratio": tune["sorted_ratio"],
-                     "points": [(p["ratio"], round(p["hash_ms"], 3), round(p["sorted_ms"], 3))
-                                for p in tune["points"]]},
+        "autotune": autotune_summary(tune),
         "kernels_one_step": head["kernels_one_step"]})
     if extras:
         line["other_workloads"] = extras

@@ -126,8 +126,15 @@ typedef struct {
   int32_t reserved[3];   /* zero */
 } mapsq_join_opts;
 
-/* What mapsq_autotune measured: per tested ratio r of sorted-side rows to
- * other-side rows, the time of one join by each algorithm. */
+/* What mapsq_autotune measured (times: best of three joins, milliseconds).
+ * Shuffle axis: per tested ratio r of sorted-side rows to other-side rows,
+ * one join by each algorithm.  Size axis: hash joins of part_rows[i] build
+ * rows (two per key) probed by four times as many rows, with and without the
+ * region partition of the build side.  Skew axis: hash joins whose keys have
+ * group[i] build rows each (2^20 build rows, 2^20 probe rows, every probe row
+ * matching a whole group), written by the dense write (a thread per probe
+ * row) or by the partitioned write (output tiles spread over all SMs).  Size
+ * axis points: 2^16, 2^18, 2^20, 2^22 and 2^24 build rows. */
 typedef struct {
   uint32_t sorted_ratio;   /* chosen: AUTO takes SORTED from this ratio up (0xFFFFFFFF = never) */
   uint32_t points;         /* tested ratios */
@@ -135,17 +142,34 @@ typedef struct {
   double hash_ms[12];
   double sorted_ms[12];
   uint64_t sorted_rows;    /* rows of the sorted side in the test joins */
+  uint64_t part_min_build; /* chosen: hash builds of at least this many rows are partitioned (UINT64_MAX = never) */
+  uint32_t part_points;
+  uint32_t dense_max;      /* chosen: the dense write for joins of at most this many matches per probe row
+                              on average (and at most 64 in any row) */
+  uint64_t part_rows[6];
+  double part_on_ms[6];
+  double part_off_ms[6];
+  uint32_t dense_points;
+  uint32_t group[6];
+  double dense_ms[6];
+  double partitioned_ms[6];
 } mapsq_autotune_result;
 
-/* Autotune the AUTO choice between the hash and the sorted join on this GPU
- * (two ways of Algorithm 1's Sort step; the choice is this library's):
- * joins a sorted side of ``sorted_rows`` rows (0 = 2^22; keys k / 2, so every
- * key twice) with other sides of sorted_rows / r rows (keys uniform over the
- * same range) for r = 1, 2, 4, ..., 2048, timing each algorithm (best of
- * three, host synchronisation included), and sets the context's sorted ratio
- * to the smallest r from which SORTED is never slower.  ``out`` may be NULL.
- * Uses about 40 bytes per sorted row of device memory.  Errors: BUSY
- * (serving), OOM, BUDGET, CUDA. */
+/* Autotune the context's join choices on this GPU (the paper has no
+ * counterpart; every choice computes Algorithm 1's same result):
+ * (1) hash vs sorted join (two ways of Algorithm 1's Sort step): joins a
+ * sorted side of ``sorted_rows`` rows (0 = 2^22; keys k / 2, so every key
+ * twice) with other sides of sorted_rows / r rows (keys uniform over the same
+ * range) for r = 1, 2, 4, ..., 2048 and sets the sorted ratio to the smallest r
+ * from which SORTED is never slower; (2) per build size, whether a hash
+ * build is partitioned by region first (build sides of 2^16 to 2^22 rows):
+ * the smallest size from which partitioning is never slower; (3) per skew
+ * (rows per key group, 4 to 64), the dense or the partitioned write: the
+ * dense write up to the largest group size at which it is not slower, applied
+ * to a join's mean number of matches per probe row.  Times are the best of
+ * three joins, host synchronisation included.  ``out`` may be NULL.  Uses
+ * about 2.5 GB of device memory at most.  Errors: BUSY (serving), OOM,
+ * BUDGET, CUDA. */
 MAPSQ_API int mapsq_autotune(mapsq_ctx* ctx, uint64_t sorted_rows, mapsq_autotune_result* out);
 
 /* Set the context's sorted ratio directly (what mapsq_autotune measures; the
@@ -201,6 +225,12 @@ MAPSQ_API int mapsq_set_stream(mapsq_ctx* ctx, void* cuda_stream);
 
 /* Description of the last error on this context (never NULL). */
 MAPSQ_API const char* mapsq_last_error(const mapsq_ctx* ctx);
+
+/* Which build of the library this is: "sm_103a", or "sm_103a checked" for
+ * libmapsq_checked.so, whose kernels check their device indexes (a failed
+ * check sets a bit of the device status word, skips the access and makes the
+ * call return MAPSQ_ERR_CUDA; joins then synchronise once more).  Never NULL. */
+MAPSQ_API const char* mapsq_build_info(void);
 
 /* Name of a status code. */
 MAPSQ_API const char* mapsq_strerror(int status);

@@ -1,7 +1,9 @@
-"""Build libmapsq.so (CUDA for sm_103a) in-tree.
+"""Build libmapsq.so (CUDA for sm_103a) in-tree, and libmapsq_checked.so, the
+same sources with device bounds checks (-DMAPSQ_CHECKED).
 
-Each translation unit is compiled by nvcc in parallel, then linked into one
-shared library next to this file.  No CMake; a minute or two on a cold cache.
+Each translation unit of both libraries is compiled by nvcc in parallel, then
+linked into one shared library each, next to this file.  No CMake; a minute or
+two on a cold cache.
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmapsq.so")
+LIB_CHECKED = os.path.join(PKG, "libmapsq_checked.so")
 
 SOURCES = ["api.cu", "prim.cu", "store.cu", "scan.cu", "join.cu", "query.cu", "serve.cu", "autotune.cu", "select.cu", "star.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -45,15 +48,19 @@ def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "mapsq.h"))
-    objs = []
-    jobs = []
     cc = nvcc()
-    for src in SOURCES:
-        s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
-        objs.append(o)
-        if not _newer(o, [s, __file__] + headers):
-            jobs.append([cc] + flags(extra) + ["-c", s, "-o", o])
+    variants = [(LIB, BUILD, list(extra)), (LIB_CHECKED, os.path.join(BUILD, "checked"), list(extra) + ["-DMAPSQ_CHECKED"])]
+    jobs, links = [], []
+    for lib, obj_dir, fl in variants:
+        os.makedirs(obj_dir, exist_ok=True)
+        objs = []
+        for src in SOURCES:
+            s = os.path.join(CSRC, src)
+            o = os.path.join(obj_dir, src.replace(".cu", ".o"))
+            objs.append(o)
+            if not _newer(o, [s, __file__] + headers):
+                jobs.append([cc] + flags(fl) + ["-c", s, "-o", o])
+        links.append((lib, objs))
 
     def run(cmd):
         if verbose:
@@ -67,10 +74,11 @@ def build(verbose: bool = False, extra=()) -> str:
         for msg in ex.map(run, jobs):
             if verbose and msg:
                 print(msg, file=sys.stderr)
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp"
-        run([cc] + ARCH + ["-shared", "-o", tmp] + objs)
-        os.replace(tmp, LIB)
+    for lib, objs in links:
+        if not _newer(lib, objs):
+            tmp = lib + ".tmp"
+            run([cc] + ARCH + ["-shared", "-o", tmp] + objs)
+            os.replace(tmp, lib)
     return LIB
 
 

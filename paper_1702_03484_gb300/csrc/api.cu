@@ -225,7 +225,19 @@ int check_status(Ctx* ctx) {
   ctx->h_pinned[32] = 0;
   MQ_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream));
   if (st & 2u) return set_error(ctx, MAPSQ_ERR_TIMEOUT, "a bounded device wait gave up (status 0x%x)", st);
+  if (st & kStatusBounds) return set_error(ctx, MAPSQ_ERR_CUDA, "a device bounds check failed (status 0x%x)", st);
   return set_error(ctx, MAPSQ_ERR_CUDA, "device status 0x%x (hash table full or index out of range)", st);
+}
+
+int checked_sync(Ctx* ctx) {
+#ifdef MAPSQ_CHECKED
+  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
+#else
+  (void)ctx;
+  return MAPSQ_OK;
+#endif
 }
 
 }  // namespace mapsq
@@ -250,6 +262,14 @@ const char* mapsq_strerror(int status) {
 }
 
 const char* mapsq_last_error(const mapsq_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+const char* mapsq_build_info(void) {
+#ifdef MAPSQ_CHECKED
+  return "sm_103a checked";
+#else
+  return "sm_103a";
+#endif
+}
 
 int mapsq_create(mapsq_ctx** out, int device, const mapsq_allocator* allocator, void* cuda_stream,
                  uint64_t mem_budget_bytes) {

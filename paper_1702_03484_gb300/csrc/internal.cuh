@@ -12,9 +12,21 @@
 
 #include "mapsq.h"
 
+// Device bounds checks of the checked build (compiled with -DMAPSQ_CHECKED,
+// libmapsq_checked.so): a failed check sets bit 4 (16) of the given status
+// word and the access is skipped, never a trap; the call that launched the
+// kernel reports it after a synchronisation.  In the regular build the checks
+// are not compiled.
+#ifdef MAPSQ_CHECKED
+#define MQ_IN_BOUNDS(cond, status) ((cond) || (atomicOr((status), 16u), false))
+#else
+#define MQ_IN_BOUNDS(cond, status) true
+#endif
+
 namespace mapsq {
 
 constexpr size_t kPinnedWords = 4096;
+constexpr uint32_t kStatusBounds = 16u;  // status bit of a failed bounds check (checked build)
 
 // Kernels timed by the profiling switch (mapsq_set_profiling).
 enum KernelId {
@@ -127,6 +139,8 @@ struct mapsq_ctx {
   std::vector<mapsq::TableImpl*> live_tables;
   uint32_t sorted_ratio = 4;      // AUTO joins: sorted side rows / other side rows from which SORTED runs
   uint32_t wait_spins = 1u << 20; // polls of a bounded device wait before it gives up (mapsq_set_wait_limit)
+  uint64_t part_min_build = 1u << 16;  // hash builds of at least this many rows are partitioned first (autotuned)
+  uint64_t dense_max = 16;             // joins of at most this many matches per probe row: dense write (autotuned)
   // term dictionary for mapsq_decode (device): id i is dict_bytes[dict_off[i] .. dict_off[i + 1])
   uint64_t* dict_off = nullptr;
   char* dict_bytes = nullptr;
@@ -240,6 +254,8 @@ void server_shutdown(Ctx* ctx);
 
 // Device status word check after a synchronisation.
 int check_status(Ctx* ctx);
+// In the checked build: synchronise and report the context's status word (no-op otherwise).
+int checked_sync(Ctx* ctx);
 
 // Primitives (prim.cu).
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.

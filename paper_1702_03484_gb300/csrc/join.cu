@@ -66,7 +66,8 @@ constexpr int kHllSpan = 16;                           // row tiles per sketch C
 constexpr int kBucket = 4;
 constexpr int kPhases = 11;
 constexpr int kDenseUnroll = 4;                        // probe rows of a thread unrolled in the dense write
-constexpr uint32_t kDenseMax = 16;                     // joins of at most this many matches per probe row: dense write
+constexpr uint32_t kDenseMax = 16;                     // default crossover of the mean matches per probe row
+constexpr uint64_t kDenseCap = 64;                     // no dense write when a probe row has more matches                     // joins of at most this many matches per probe row: dense write
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
 constexpr int kSortedItems = kRowTile / kSortedThreads;
@@ -127,6 +128,7 @@ struct JoinDesc {
   int hash;                       // shared variables and both sides non-empty: the hash path runs
   int sorted;                     // the build side is sorted on its (one) key column: groups are its runs
   uint32_t bstride;               // words between a build row's values: nbv (grouped) or 1 (columns)
+  uint32_t* check;                // status word of the checked build's bounds checks
 };
 
 // Item offsets of one phase: join j owns items [first[j], first[j + 1]).
@@ -293,6 +295,7 @@ struct PartDesc {
   uint32_t* cursor;                     // kRegions: next free row of each region (starts at its offset)
   uint64_t n;
   int nkey, ncols;
+  uint32_t* check;                      // status word of the checked build's bounds checks
 };
 
 __global__ void __launch_bounds__(kPartThreads, 2) partition_kernel(const PartDesc* __restrict__ pd, const uint64_t* first,
@@ -358,7 +361,8 @@ __global__ void __launch_bounds__(kPartThreads, 2) partition_kernel(const PartDe
     __syncthreads();
     for (uint32_t q = threadIdx.x; q < n; q += kPartThreads) {
       const uint32_t reg = s_reg[q];
-      __stcg(p.dst[c] + s_gb[reg] + (q - s_lo[reg]), s_buf[q]);
+      const uint64_t at = uint64_t(s_gb[reg]) + (q - s_lo[reg]);
+      if (MQ_IN_BOUNDS(at < p.n, p.check)) __stcg(p.dst[c] + at, s_buf[q]);
     }
     __syncthreads();
   }
@@ -585,7 +589,7 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint64_t i = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
-        if (s[q] != kNoSlot)
+        if (s[q] != kNoSlot && MQ_IN_BOUNDS(pos[q] < d.nb, d.check))
           reinterpret_cast<uint2*>(d.grouped)[pos[q]] = make_uint2(__ldcs(d.bsrc[0] + i), __ldcs(d.bsrc[1] + i));
       }
       continue;
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(kThreads) hash_scatter_kernel(const JoinDesc* 
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (s[q] != kNoSlot) d.grouped[uint64_t(pos[q]) * uint32_t(nbv) + c] = x[q];
+        if (s[q] != kNoSlot && MQ_IN_BOUNDS(pos[q] < d.nb, d.check)) d.grouped[uint64_t(pos[q]) * uint32_t(nbv) + c] = x[q];
     }
   }
 }
@@ -646,8 +650,9 @@ __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(con
       const int loc = (h0 + q) * kThreads + threadIdx.x;
       const uint64_t row = base + loc;
       const uint2 g = s[q] != kNoSlot ? *group_of(t, s[q]) : make_uint2(0u, 0u);
-      if (row < np) __stcs(d.pbeg + row, g.x ? group_begin(t, s[q], g.y) : 0u);
-      s_cnt[pad(loc)] = g.x;
+      const uint32_t gbeg = g.x ? group_begin(t, s[q], g.y) : 0u;
+      if (row < np) __stcs(d.pbeg + row, gbeg);
+      s_cnt[pad(loc)] = MQ_IN_BOUNDS(uint64_t(gbeg) + g.x <= d.nb, d.check) ? g.x : 0u;
       const unsigned nz = __ballot_sync(0xffffffffu, g.x != 0);  // the warp's 32 consecutive rows
       if ((threadIdx.x & 31) == 0 && row < np) d.nzmask[row >> 5] = nz;
     }
@@ -1028,6 +1033,7 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
         if (off_at(d, i + 1) <= r) i = next_nonzero(d, i);  // ranges are contiguous: the next matching row
         s_pk[mi(q)] = uint32_t(i - ilo);
         s_bk[mi(q)] = d.pbeg[i] + uint32_t(r - off_at(d, i));
+        if (!MQ_IN_BOUNDS(i < d.np && s_bk[mi(q)] < d.nb, d.check)) s_pk[mi(q)] = s_bk[mi(q)] = 0;
       }
     }
     for (uint64_t c0 = ilo; staged && c0 < ihi; c0 += kStageRows) {
@@ -1050,6 +1056,7 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
           }
           s_pk[mi(q)] = rbase + r;
           s_bk[mi(q)] = s_beg[r] + (q - s_rel[r]) + (r == 0 ? skip : 0u);
+          if (!MQ_IN_BOUNDS(ilo + rbase + r < d.np && s_bk[mi(q)] < d.nb, d.check)) s_pk[mi(q)] = s_bk[mi(q)] = 0;
         }
       }
       __syncthreads();
@@ -1103,9 +1110,9 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
   }
 }
 
-// Write phase of a join whose probe rows have at most kDenseMax matches each
-// (16, the best of a sweep of 4, 8 and 16):
-// a thread per probe row writes that row's output rows.  Consecutive threads
+// Write phase of a join whose probe rows have few matches (on average at most
+// the autotuned crossover, none more than kDenseCap): a thread per probe row
+// writes that row's output rows.  Consecutive threads
 // own consecutive probe rows, hence consecutive output ranges, so a warp's
 // stores of a column stay within a few lines; every whole aligned run of four
 // output rows takes one 16-byte store per column.  No partition, no shared
@@ -1128,6 +1135,7 @@ __global__ void __launch_bounds__(kThreads) dense_write_kernel(const JoinDesc* _
     const uint32_t c = uint32_t(e - o);
     if (!c) continue;
     const uint32_t g = d.pbeg[i];
+    if (!MQ_IN_BOUNDS(e <= d.T && uint64_t(g) + c <= d.nb, d.check)) continue;
     for (int col = 0; col < ncols; ++col) {
       uint32_t* __restrict__ dst = d.out[col] + o;
       const uint32_t* __restrict__ src = d.src[col];
@@ -1264,7 +1272,15 @@ struct BatchJoin {
   uint32_t k = 0;
   int algorithm = MAPSQ_JOIN_AUTO;
   uint32_t sorted_ratio = kSortedRatio;
+  uint64_t part_min_build = kHllMinBuild;  // build rows from which a hash build is partitioned first
+  uint64_t dense_max = kDenseMax;          // largest mean matches per probe row for the dense write
 
+  // The context's autotuned choices (hash vs sorted, partitioned build, dense write).
+  void tune_from(const Ctx* c) {
+    sorted_ratio = c->sorted_ratio;
+    part_min_build = c->part_min_build;
+    dense_max = c->dense_max;
+  }
   int fail(int code, const char* what) { return ctx ? set_error(ctx, code, "%s", what) : code; }
   int cuda(cudaError_t e, const char* what) {
     return e == cudaSuccess ? MAPSQ_OK : (ctx ? cuda_fail(ctx, e, what, __FILE__, __LINE__) : MAPSQ_ERR_CUDA);
@@ -1337,6 +1353,7 @@ struct BatchJoin {
       if (pl.nb >= (uint64_t(1) << 31)) return fail(MAPSQ_ERR_UNSUPPORTED, "build side of 2^31 rows or more");
       if (pl.cross && pl.nb && pl.np > UINT64_MAX / pl.nb) return fail(MAPSQ_ERR_BUDGET, "cross product overflows 64 bits");
       JoinDesc& d = descs[j];
+      d.check = status;  // the word given at construction (the batch's own word replaces ``status`` later)
       d.nb = pl.nb;
       d.np = pl.np;
       d.cross = pl.cross;
@@ -1397,7 +1414,8 @@ struct BatchJoin {
           plans[j].region_off[r] = run;
           run += w[kHllRegs + r];
         }
-        plans[j].part = run == pl_rows(j);  // the histogram covers every row (it always should)
+        // partitioned from the autotuned build size on (when the histogram covers every row, as it should)
+        plans[j].part = run == pl_rows(j) && plans[j].nb >= part_min_build;
       }
     }
     for (auto& pl : plans) {
@@ -1518,6 +1536,7 @@ struct BatchJoin {
       PartDesc& pd = pdescs[j];
       pd.nkey = pl.lay.nkey;
       pd.n = pl.nb;
+      pd.check = d.check;
       pd.cursor = d_cursor + size_t(j) * kRegions;
       for (int q = 0; q < pl.lay.nkey; ++q) pd.src[pd.ncols++] = pl.B->col[pl.bkey[q]];
       for (int c = pl.lay.nkey; c < pl.lay.ncols; ++c)
@@ -1696,7 +1715,7 @@ struct BatchJoin {
       if (pl.cross) {
         cr[j] = ntiles;
         cbytes += 4.0 * pl.T * pl.lay.ncols + in;
-      } else if (pl.maxc <= kDenseMax) {
+      } else if (pl.T <= dense_max * pl.np && pl.maxc <= kDenseCap) {  // few matches per probe row on average
         dn[j] = ceil_div(pl.np, kRowTile);
         dbytes += 4.0 * pl.T * pl.lay.ncols + in;
       } else {
@@ -1741,7 +1760,8 @@ struct BatchJoin {
       launched();
       done(r, cbytes);
     }
-    return cuda(cudaGetLastError(), "write phases");
+    MQ_TRY(cuda(cudaGetLastError(), "write phases"));
+    return ctx ? checked_sync(ctx) : MAPSQ_OK;
   }
 };
 
@@ -1755,7 +1775,7 @@ int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_ta
   Scratch scratch(ctx);
   BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
   bj.algorithm = opts ? opts->algorithm : MAPSQ_JOIN_AUTO;
-  bj.sorted_ratio = ctx->sorted_ratio;
+  bj.tune_from(ctx);
   MQ_TRY(bj.prepare(k, L, R));
   MQ_TRY(bj.count());
   std::vector<TableImpl*> tabs(k, nullptr);
@@ -1784,7 +1804,7 @@ int join_batch_admit(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const ma
   if (k == 0) return MAPSQ_OK;
   Scratch scratch(ctx);
   BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
-  bj.sorted_ratio = ctx->sorted_ratio;
+  bj.tune_from(ctx);
   MQ_TRY(bj.prepare(k, L, R));
   MQ_TRY(bj.count());
   // admission in order: result tables are written while they fit in the budget
@@ -1860,7 +1880,7 @@ int join_to_host(Ctx* ctx, const mapsq_table* L, const mapsq_table* R, const map
       Scratch scratch(ctx);
       BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
       bj.algorithm = opts ? opts->algorithm : MAPSQ_JOIN_AUTO;
-      bj.sorted_ratio = ctx->sorted_ratio;
+      bj.tune_from(ctx);
       rc = bj.prepare(1, &A, &B);
       if (rc == MAPSQ_OK) rc = bj.count();
       if (rc == MAPSQ_OK) rows = bj.plans[0].T;

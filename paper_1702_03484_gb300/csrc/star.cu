@@ -43,6 +43,7 @@ struct StarDesc {
   uint32_t* cnt;                        // n[0]: output rows of driving row i
   const uint64_t* off;                  // n[0] + 1: exclusive prefix sums of cnt
   uint64_t T;
+  uint32_t* check;                      // status word of the checked build's bounds checks
 };
 
 __device__ __forceinline__ uint64_t lower_bound_key(const uint32_t* __restrict__ a, uint64_t n, uint32_t x) {
@@ -113,6 +114,9 @@ __global__ void __launch_bounds__(kStarThreads) star_write_kernel(StarDesc d) {
         row[j] = d.lo[(j - 1) * n0 + i] + r % L;
         r /= L;
       }
+      bool ok = true;
+      for (int j = 0; j < d.k; ++j) ok = ok && MQ_IN_BOUNDS(row[j] < d.n[j], d.check);
+      if (!ok) continue;
       for (int c = 0; c < d.ncols; ++c) d.out[c][t] = __ldg(d.src[c] + row[d.tab[c]]);
     }
   }
@@ -187,6 +191,7 @@ int join_star(Ctx* ctx, uint32_t k, const mapsq_table* const* tabs, int32_t key_
   }
   StarDesc d{};
   d.k = int(k);
+  d.check = ctx->d_status;
   std::vector<int> order;  // table of each StarDesc slot
   order.push_back(driver);
   for (uint32_t j = 0; j < k; ++j)
@@ -251,6 +256,11 @@ int join_star(Ctx* ctx, uint32_t k, const mapsq_table* const* tabs, int32_t key_
       table_release(ctx, t);
       return cuda_fail(ctx, e, "star_write_kernel", __FILE__, __LINE__);
     }
+  }
+  const int rc = checked_sync(ctx);
+  if (rc != MAPSQ_OK) {
+    table_release(ctx, t);
+    return rc;
   }
   *out = t;
   return MAPSQ_OK;

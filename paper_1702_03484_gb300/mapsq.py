@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmapsq.so")
+# MAPSQ_LIB selects another build of the library (libmapsq_checked.so: the
+# kernels check their device indexes)
+LIB_PATH = os.environ.get("MAPSQ_LIB") or os.path.join(_HERE, "libmapsq.so")
 
 MAX_VARS = 16
 VAR_S, VAR_P, VAR_O = 1, 2, 4
@@ -50,7 +52,11 @@ class JoinOpts(C.Structure):
 
 class AutotuneResult(C.Structure):
     _fields_ = [("sorted_ratio", C.c_uint32), ("points", C.c_uint32), ("ratio", C.c_uint32 * 12),
-                ("hash_ms", C.c_double * 12), ("sorted_ms", C.c_double * 12), ("sorted_rows", C.c_uint64)]
+                ("hash_ms", C.c_double * 12), ("sorted_ms", C.c_double * 12), ("sorted_rows", C.c_uint64),
+                ("part_min_build", C.c_uint64), ("part_points", C.c_uint32), ("dense_max", C.c_uint32),
+                ("part_rows", C.c_uint64 * 6), ("part_on_ms", C.c_double * 6), ("part_off_ms", C.c_double * 6),
+                ("dense_points", C.c_uint32), ("group", C.c_uint32 * 6), ("dense_ms", C.c_double * 6),
+                ("partitioned_ms", C.c_double * 6)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -86,6 +92,7 @@ _SIGNATURES = {
     "mapsq_set_stream": (C.c_int, [_P, _P]),
     "mapsq_last_error": (C.c_char_p, [_P]),
     "mapsq_strerror": (C.c_char_p, [C.c_int]),
+    "mapsq_build_info": (C.c_char_p, []),
     "mapsq_load_triples": (C.c_int, [_P, _P, _P, _P, C.c_uint64, C.c_int]),
     "mapsq_store_info": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)]),
     "mapsq_scan_pattern": (C.c_int, [_P, C.POINTER(Pattern), C.POINTER(_TP)]),
@@ -283,6 +290,11 @@ def mapsq_join_star(ctx, tables, key_var):
     return out
 
 
+def mapsq_build_info():
+    """Which build of the library is loaded ("sm_103a" or "sm_103a checked")."""
+    return lib().mapsq_build_info().decode()
+
+
 def mapsq_set_wait_limit(ctx, spins):
     _check(ctx, lib().mapsq_set_wait_limit(ctx, spins))
 
@@ -422,7 +434,12 @@ def mapsq_autotune(ctx, sorted_rows=0):
     _check(ctx, lib().mapsq_autotune(ctx, sorted_rows, C.byref(r)))
     n = r.points
     return {"sorted_ratio": r.sorted_ratio, "sorted_rows": r.sorted_rows,
-            "points": [{"ratio": r.ratio[i], "hash_ms": r.hash_ms[i], "sorted_ms": r.sorted_ms[i]} for i in range(n)]}
+            "points": [{"ratio": r.ratio[i], "hash_ms": r.hash_ms[i], "sorted_ms": r.sorted_ms[i]} for i in range(n)],
+            "part_min_build": r.part_min_build, "dense_max": r.dense_max,
+            "size_points": [{"build_rows": r.part_rows[i], "partitioned_ms": r.part_on_ms[i],
+                             "plain_ms": r.part_off_ms[i]} for i in range(r.part_points)],
+            "skew_points": [{"group_rows": r.group[i], "dense_ms": r.dense_ms[i],
+                             "partitioned_write_ms": r.partitioned_ms[i]} for i in range(r.dense_points)]}
 
 
 def mapsq_set_sorted_ratio(ctx, ratio):

@@ -41,6 +41,19 @@ def test_library_exports_every_declared_symbol(built):
     assert set(declared()) <= exported
 
 
+def test_checked_build_exports_the_same_boundary(built):
+    """libmapsq_checked.so (device bounds checks) exports the same calls and
+    says which build it is, without any device call."""
+    checked = os.path.join(os.path.dirname(built), "libmapsq_checked.so")
+    lib = ctypes.CDLL(checked)
+    assert not [n for n in declared() if not hasattr(lib, n)]
+    lib.mapsq_build_info.restype = ctypes.c_char_p
+    assert lib.mapsq_build_info() == b"sm_103a checked"
+    plain = ctypes.CDLL(built)
+    plain.mapsq_build_info.restype = ctypes.c_char_p
+    assert plain.mapsq_build_info() == b"sm_103a"
+
+
 def test_binding_covers_every_declared_symbol(built):
     from paper_1702_03484_gb300 import mapsq
     assert set(declared()) == set(mapsq._SIGNATURES)

@@ -342,8 +342,19 @@ def test_autotune_sets_ratio_and_joins_stay_exact():
         assert all(p["hash_ms"] > 0 and p["sorted_ms"] > 0 for p in res["points"])
         ratio = res["sorted_ratio"]
         assert ratio == 0xFFFFFFFF or ratio in [p["ratio"] for p in res["points"]]
+        # size axis: 2^16 .. 2^22 build rows; skew axis: groups of 4 .. 64 rows
+        assert [p["build_rows"] for p in res["size_points"]] == [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24]
+        assert [p["group_rows"] for p in res["skew_points"]] == [4, 8, 16, 32, 64]
+        assert res["part_min_build"] == (1 << 64) - 1 or res["part_min_build"] in [p["build_rows"]
+                                                                                    for p in res["size_points"]]
+        assert 1 <= res["dense_max"] <= 64
         L, R = gen.pairwise_uniform(seed=1)
         join_and_check(c, L, R, "after autotune")
+        # the choices apply to later joins: a large build side and large key groups stay exact
+        r = gen.Rng(71)
+        B = gen.Table([0, 2], [r.below(1 << 17, 3000).astype(np.uint32), r.u32(1 << 17)])
+        P = gen.Table([0, 1], [r.below(9000, 3000).astype(np.uint32), r.u32(9000)])
+        join_and_check(c, P, B, "build of 2^17 rows, about 44 rows per key, after autotune")
         with pytest.raises(MapsqError):
             c.autotune(sorted_rows=100)
 
