@@ -6,8 +6,9 @@ frequencies on A, exactly 2^28 output rows (one step = one mapsq_join).
 Metric: output bindings/s (one binding = one output row).  After the headline,
 the same line carries the other join workloads measured in the same process
 (``other_workloads``): the 256-join uneven batch (batched against plain), the
-32 BGPs over a 1e7-triple university graph (plain against batched) and the
-16384 x 8192 pairwise join.
+32 BGPs over a 1e7-triple university graph (plain against batched), the
+16384 x 8192 pairwise join and a 3-second served stream over the 1e8-triple
+graph (p50/p99 latency, against the same queries one after another).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload skewed_join|university_bgp|pairwise_uniform|uneven_batch|serving]
@@ -715,7 +716,7 @@ def _ref_init(workload, size):
 
 
 def _ref_config(_):
-    return _REF.name, _REF.config
+    return _REF.name, _REF.config, _REF.oracle_unit
 
 
 def _ref_sample(job):
@@ -742,7 +743,7 @@ def run_reference(args):
     if args.workload == "serving":
         cores = min(cores, 4)
     with mp.get_context("spawn").Pool(cores, initializer=_ref_init, initargs=(args.workload, args.size)) as pool:
-        name, config = pool.map(_ref_config, [0])[0]
+        name, config, unit_desc = pool.map(_ref_config, [0])[0]
         for i in range(args.warmup):
             pool.map(_ref_sample, [(i * cores + c, cores * (args.warmup + args.steps), 0.5) for c in range(cores)])
         rows, units, t0 = 0, 0, time.perf_counter()
@@ -754,7 +755,7 @@ def run_reference(args):
         dt = time.perf_counter() - t0
     value = rows / dt
     sample = (f"per step about 2 s of the {name} workload on each of {cores} host processes ({units} units in "
-              f"{args.steps} steps; units are BGPs or join slices), oracle in numpy")
+              f"{args.steps} steps; units: {unit_desc}), oracle in numpy")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -847,6 +848,29 @@ def whole_step_roofline(w, rows_per_step, ms_per_step, peak):
 EXTRAS = ("uneven_batch", "university_bgp", "pairwise_uniform")
 
 
+def measure_serving_short(ctx, steps=2, pool=256):
+    """A short served stream over the 1e8-triple graph (the serving config with
+    a smaller BGP pool and ``steps`` x 1.5 s of Poisson arrivals at 2000
+    queries/s): latency percentiles, throughput, and the same queries one
+    mapsq_query after another (2 s sample)."""
+    w = Serving(pool=pool)
+    w.setup_gpu(ctx)
+    w.serve(ctx, 1, part=1)  # warm-up stream
+    rows, wall, dev_ms, _, _, counters, idx = w.serve(ctx, steps, part=2)
+    s_rows, s_n, s_ms = w.run_serial(ctx, idx, budget_s=2.0)
+    res = {"value": rows / (dev_ms / 1000.0), "unit": UNIT, "queries": counters["submitted"],
+           "completed": counters["completed"], "failed": counters["failed"], "p50_ms": counters["p50_ms"],
+           "p99_ms": counters["p99_ms"], "mean_ms": counters["mean_ms"], "achieved_qps": counters["submitted"] / wall,
+           "rounds": counters["rounds"], "batched_joins": counters["batched_joins"],
+           "preempted": counters["preempted"], "wall_s": wall,
+           "serial_plain": {"value": s_rows / (s_ms / 1000.0) if s_ms else None, "unit": UNIT, "queries": s_n,
+                            "ms_per_query": s_ms / max(s_n, 1)},
+           "config": dict(w.config, bgp_pool=pool, steps=steps),
+           "form": "mapsq_serve_*: continuous batching of the queries in flight, 40 GB admission budget"}
+    w.release(ctx)
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -896,6 +920,7 @@ def run_ours(args):
                     r["other_over_this"] = r["other_form"]["value"] / r["value"]
                 extras[name] = r
                 x.release(ctx)
+            extras["serving"] = measure_serving_short(ctx)
 
     t_max, rows_all = combine_ranks(total_ms, rows, world, dev)
     if world > 1:
