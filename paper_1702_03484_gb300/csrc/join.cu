@@ -55,7 +55,7 @@ constexpr int kStageRows = 1800;                       // probe rows per stage c
 constexpr int kWriteBlocks = 4;                        // write CTAs per SM (register budget)
 constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
 constexpr int kProbeIn = 2;                            // probe rows in flight per thread
-constexpr int kProbeBlocks = 6;                        // probe CTAs per SM (register budget)
+constexpr int kProbeBlocks = 5;                        // probe CTAs per SM (register budget)
 constexpr int kEarlyTiles = 64;                        // joins of up to this many write tiles are partitioned by the count scan
 constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
 constexpr int kWriteSmem = int(sizeof(uint32_t)) * (2 * kStageRows + 1 + 2 * kMapWords);  // write kernel's dynamic shared memory
@@ -627,16 +627,20 @@ __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(con
   const uint64_t base = tile * kRowTile;
   const uint64_t np = d.np;
   auto pad = [](int i) { return i + (i >> 5); };
+  // every key of the thread's rows first: the streamed loads overlap the lookups
+  uint64_t keys[kRowItems];
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    const uint64_t row = base + uint64_t(q) * kThreads + threadIdx.x;
+    keys[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
+  }
 #pragma unroll
   for (int h0 = 0; h0 < kRowItems; h0 += kProbeIn) {
     uint64_t key[kProbeIn];
     uint32_t b[kProbeIn], s[kProbeIn];
     ulonglong2 k01[kProbeIn], k23[kProbeIn];
 #pragma unroll
-    for (int q = 0; q < kProbeIn; ++q) {
-      const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
-      key[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
-    }
+    for (int q = 0; q < kProbeIn; ++q) key[q] = keys[h0 + q];
 #pragma unroll
     for (int q = 0; q < kProbeIn; ++q)
       if (key[q] != kEmptyKey) load_bucket(t, key[q], &b[q], &k01[q], &k23[q]);
