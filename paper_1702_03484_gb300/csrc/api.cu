@@ -1,6 +1,7 @@
 // C ABI entry points: contexts, memory, tables, profiling, and the BGP planner
 // (the host side of the paper's CPU/GPU coprocessing split, Section 2).
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <new>
 
@@ -202,10 +203,50 @@ int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes) {
 
 int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count) {
   if (count < 1 || count > 32) return set_error(ctx, MAPSQ_ERR_INVALID, "read_u64 of %d words", count);
-  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned, dptr, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost, ctx->stream));
-  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
-  memcpy(host, ctx->h_pinned, sizeof(uint64_t) * count);
+  return read_words(ctx, dptr, size_t(count), host);
+}
+
+namespace {
+
+// Copies n words and the status word to mapped host memory, then (after a
+// system-scope fence, so that the host sees them first) the sequence number.
+__global__ void publish_kernel(const uint64_t* __restrict__ src, uint32_t n, const uint32_t* __restrict__ status,
+                               uint64_t* dst, uint64_t seq) {
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[2 + i] = src[i];
+  if (threadIdx.x == 0) dst[1] = *status;
+  __threadfence_system();
+  __syncthreads();
+  if (threadIdx.x == 0) *reinterpret_cast<volatile uint64_t*>(dst) = seq;
+}
+
+constexpr auto kPublishPoll = std::chrono::microseconds(500);  // then block in cudaStreamSynchronize
+
+}  // namespace
+
+int read_words(Ctx* ctx, const void* dptr, size_t n, uint64_t* host) {
+  if (n > kReadWords) return set_error(ctx, MAPSQ_ERR_INVALID, "read of %zu words", n);
+  const uint64_t seq = ++ctx->mapped_seq;
+  publish_kernel<<<1, 256, 0, ctx->stream>>>(static_cast<const uint64_t*>(dptr), uint32_t(n), ctx->d_status,
+                                             ctx->d_mapped, seq);
+  ++ctx->launches;
+  MQ_CUDA(cudaGetLastError());
+  const auto t0 = std::chrono::steady_clock::now();
+  bool seen = false;
+  for (uint32_t i = 1;; ++i) {
+    if (__atomic_load_n(ctx->h_mapped, __ATOMIC_ACQUIRE) == seq) {
+      seen = true;
+      break;
+    }
+    if (!(i & 63) && std::chrono::steady_clock::now() - t0 > kPublishPoll) break;
+  }
+  if (!seen) {
+    MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (__atomic_load_n(ctx->h_mapped, __ATOMIC_ACQUIRE) != seq)
+      return set_error(ctx, MAPSQ_ERR_CUDA, "published read %llu missing after synchronisation",
+                       (unsigned long long)seq);
+  }
+  if (n) memcpy(host, ctx->h_mapped + 2, n * sizeof(uint64_t));
+  ctx->h_pinned[32] = ctx->h_mapped[1] & 0xFFFFFFFFu;
   return check_status(ctx);
 }
 
@@ -289,6 +330,7 @@ int mapsq_create(mapsq_ctx** out, int device, const mapsq_allocator* allocator, 
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->h_mapped) cudaFreeHost(ctx->h_mapped);
     delete ctx;
     return code;
   };
@@ -310,6 +352,12 @@ int mapsq_create(mapsq_ctx** out, int device, const mapsq_allocator* allocator, 
   }
   if (cudaMallocHost(&ctx->h_pinned, kPinnedWords * sizeof(uint64_t)) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
   memset(ctx->h_pinned, 0, kPinnedWords * sizeof(uint64_t));
+  if (cudaHostAlloc(&ctx->h_mapped, kMappedWords * sizeof(uint64_t), cudaHostAllocMapped) != cudaSuccess)
+    return fail(MAPSQ_ERR_CUDA);
+  memset(ctx->h_mapped, 0, kMappedWords * sizeof(uint64_t));
+  void* dm = nullptr;
+  if (cudaHostGetDevicePointer(&dm, ctx->h_mapped, 0) != cudaSuccess) return fail(MAPSQ_ERR_CUDA);
+  ctx->d_mapped = static_cast<uint64_t*>(dm);
   void* st = nullptr;
   rc = dev_alloc(ctx, 256, &st);
   if (rc != MAPSQ_OK) return fail(rc);
@@ -338,6 +386,7 @@ int mapsq_destroy(mapsq_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->h_mapped) cudaFreeHost(ctx->h_mapped);
   for (int s = 0; s < Ctx::kStageSlots; ++s) {
     if (ctx->h_stage[s]) cudaFreeHost(ctx->h_stage[s]);
     if (ctx->stage_done[s]) cudaEventDestroy(ctx->stage_done[s]);
@@ -492,9 +541,7 @@ int mapsq_sync(mapsq_ctx* ctx) {
   if (!ctx) return MAPSQ_ERR_INVALID;
   std::lock_guard<std::recursive_mutex> cl(ctx->mu);
   MQ_CUDA(cudaSetDevice(ctx->device));
-  MQ_CUDA(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
-  return check_status(ctx);
+  return read_words(ctx, nullptr, 0, nullptr);  // every queued operation has run once it returns
 }
 
 int mapsq_set_wait_limit(mapsq_ctx* ctx, uint32_t spins) {

@@ -26,6 +26,8 @@
 namespace mapsq {
 
 constexpr size_t kPinnedWords = 4096;
+constexpr size_t kReadWords = 4096;      // words one published read carries (read_words)
+constexpr size_t kMappedWords = 2 + kReadWords;
 constexpr uint32_t kStatusBounds = 16u;  // status bit of a failed bounds check (checked build)
 
 // Kernels timed by the profiling switch (mapsq_set_profiling).
@@ -123,6 +125,11 @@ struct mapsq_ctx {
   mapsq::Store store;
   uint32_t* d_status = nullptr;    // device status word: 0 = fine
   uint64_t* h_pinned = nullptr;    // pinned buffer for device->host reads (kPinnedWords words)
+  // host memory the device writes directly (mapped): [0] sequence number of
+  // the last published read, [1] status word, [2..] the read's words
+  uint64_t* h_mapped = nullptr;
+  uint64_t* d_mapped = nullptr;    // the same memory's device address
+  uint64_t mapped_seq = 0;
   // ring of pinned staging buffers for host->device uploads; an upload reuses a
   // buffer only after the copy that last read it has run
   static constexpr int kStageSlots = 8;
@@ -241,6 +248,12 @@ int stage_upload(Ctx* ctx, void* dst, const void* src, size_t bytes);
 
 // Read a few 64-bit words back from the device (synchronises the stream).
 int read_u64(Ctx* ctx, const void* dptr, uint64_t* host, int count);
+// ``n`` (at most kReadWords) 64-bit words at ``dptr`` into host[0, n), with the
+// status word checked, once every earlier operation of the stream has run: a
+// one-block kernel writes them and a sequence number into mapped host memory,
+// the host polls that number for a short while, then falls back to a stream
+// synchronisation (long steps, and errors).  Costs one launch and no copy.
+int read_words(Ctx* ctx, const void* dptr, size_t n, uint64_t* host);
 
 // Frees the term dictionary (mapsq_dict_load, mapsq_destroy).
 void dict_release(Ctx* ctx);

@@ -67,7 +67,7 @@ constexpr int kBucket = 4;
 constexpr int kPhases = 11;
 constexpr int kDenseUnroll = 4;                        // probe rows of a thread unrolled in the dense write
 constexpr uint32_t kDenseMax = 16;                     // default crossover of the mean matches per probe row
-constexpr uint64_t kDenseCap = 64;                     // no dense write when a probe row has more matches                     // joins of at most this many matches per probe row: dense write
+constexpr uint64_t kDenseCap = 64;                     // no dense write when a probe row has more matches
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
 constexpr int kSortedItems = kRowTile / kSortedThreads;
@@ -84,7 +84,8 @@ enum Phase { PH_HLL = 0, PH_INSERT, PH_SLOTS, PH_SCATTER, PH_COUNT, PH_PART, PH_
              PH_REGION };
 
 // Open-addressing table of the build side's distinct keys: ``keys`` holds M
-// 64-bit keys in buckets of 4 (one 32-byte sector), probed bucket after bucket
+// 64-bit keys in buckets of 4 (one 32-byte sector, read by one 32-byte load),
+// probed bucket after bucket
 // from the key's home bucket; ``group`` holds, per slot, the key group's size
 // and its first row inside its tile of kRowTile slots (the tile's start is
 // slot_base[slot / kRowTile]).  The all-ones key marks an empty slot; the one
@@ -180,12 +181,26 @@ __device__ __forceinline__ uint64_t* bucket_keys(const HashTable& t, uint32_t b)
 // Group entry {count, begin within the slot tile} of slot s.
 __device__ __forceinline__ uint2* group_of(const HashTable& t, uint32_t s) { return t.group + s; }
 
+// The four keys of a bucket in one 32-byte load (a bucket is 32-byte aligned):
+// read-only through the non-coherent path (probes), or at L2 (inserts, whose
+// buckets other threads fill meanwhile).
+__device__ __forceinline__ void ld_bucket_nc(const uint64_t* p, ulonglong2* k01, ulonglong2* k23) {
+  asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(k01->x), "=l"(k01->y), "=l"(k23->x), "=l"(k23->y)
+               : "l"(p));
+}
+
+__device__ __forceinline__ void ld_bucket_cg(const uint64_t* p, ulonglong2* k01, ulonglong2* k23) {
+  asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(k01->x), "=l"(k01->y), "=l"(k23->x), "=l"(k23->y)
+               : "l"(p)
+               : "memory");
+}
+
 __device__ __forceinline__ void load_bucket(const HashTable& t, uint64_t key, uint32_t* b, ulonglong2* k01,
                                             ulonglong2* k23) {
   *b = home_bucket(key, t.M);
-  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(bucket_keys(t, *b));
-  *k01 = __ldg(p);
-  *k23 = __ldg(p + 1);
+  ld_bucket_nc(bucket_keys(t, *b), k01, k23);
 }
 
 // Slot of ``key`` in the table, or kNoSlot, starting from its home bucket
@@ -205,9 +220,7 @@ __device__ __forceinline__ uint32_t find_slot(const HashTable& t, uint64_t key, 
       return (hit >> j) & 1u ? b * kBucket + j : kNoSlot;
     }
     b = b + 1 == nbk ? 0 : b + 1;
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(bucket_keys(t, b));
-    k01 = __ldg(p);
-    k23 = __ldg(p + 1);
+    ld_bucket_nc(bucket_keys(t, b), &k01, &k23);
   }
   return kNoSlot;
 }
@@ -403,8 +416,8 @@ __global__ void __launch_bounds__(kThreads, 8) hash_insert_kernel(const JoinDesc
         uint32_t b = home_bucket(key, t.M);
         for (uint32_t n = 0; n < nbk && s == kNoSlot; ++n) {
           uint64_t* bkt = bucket_keys(t, b);
-          const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt));
-          const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2*>(bkt) + 1);
+          ulonglong2 k01, k23;
+          ld_bucket_cg(bkt, &k01, &k23);
           const uint64_t kk[4] = {k01.x, k01.y, k23.x, k23.y};
 #pragma unroll
           for (int q = 0; q < kBucket; ++q) {
@@ -1643,19 +1656,23 @@ struct BatchJoin {
       if (attempt) mem->rewind(mark);
       MQ_TRY(allocate());
       MQ_TRY(count_phases());  // its upload zeroes the status word
-      // one copy: status word, work counter, row counts and largest counts
+      // one read: status word, work counter, row counts and largest counts
+      // (and the context's status word: an earlier call's write phase may have set it)
       host.assign(2 + 2 * size_t(k), 0);
-      // through the context's pinned buffer when it is large enough (a pageable copy is slower)
-      // (words 0-63 of it are left to read_u64 and the status word)
-      uint64_t* dst = ctx && host.size() + 64 <= kPinnedWords ? ctx->h_pinned + 64 : host.data();
-      MQ_TRY(cuda(cudaMemcpyAsync(dst, d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
-      // the context's status word too: an earlier call's write phase may have set it
-      if (ctx)
-        MQ_TRY(cuda(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                                    stream), "readback"));
-      MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
-      if (dst != host.data()) memcpy(host.data(), dst, host.size() * 8);
-      if (ctx) MQ_TRY(check_status(ctx));
+      if (ctx && host.size() <= kReadWords) {
+        MQ_TRY(read_words(ctx, d_tail, host.size(), host.data()));
+      } else {
+        // through the context's pinned buffer when it is large enough (a pageable copy is slower)
+        // (words 0-63 of it are left to read_u64 and the status word)
+        uint64_t* dst = ctx && host.size() + 64 <= kPinnedWords ? ctx->h_pinned + 64 : host.data();
+        MQ_TRY(cuda(cudaMemcpyAsync(dst, d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
+        if (ctx)
+          MQ_TRY(cuda(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                      stream), "readback"));
+        MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
+        if (dst != host.data()) memcpy(host.data(), dst, host.size() * 8);
+        if (ctx) MQ_TRY(check_status(ctx));
+      }
       const uint32_t st = uint32_t(host[0]);
       if (st & 1u) {
         // a distinct-key estimate far too low: rebuild every table at two slots per build row

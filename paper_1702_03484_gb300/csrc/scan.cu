@@ -166,10 +166,14 @@ int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* ou
   prof_end(ctx, rec, double(n) * 32);
   MQ_CUDA(cudaGetLastError());
   std::vector<uint64_t> h(2 * size_t(n));
-  uint64_t* dst = h.size() <= kPinnedWords ? ctx->h_pinned : h.data();  // pinned when it fits
-  MQ_CUDA(cudaMemcpyAsync(dst, dout, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
-  MQ_CUDA(cudaStreamSynchronize(ctx->stream));
-  if (dst != h.data()) memcpy(h.data(), dst, h.size() * sizeof(uint64_t));
+  if (h.size() <= kReadWords) {
+    MQ_TRY(read_words(ctx, dout, h.size(), h.data()));
+  } else {
+    uint64_t* dst = h.size() <= kPinnedWords ? ctx->h_pinned : h.data();  // pinned when it fits
+    MQ_CUDA(cudaMemcpyAsync(dst, dout, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    MQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (dst != h.data()) memcpy(h.data(), dst, h.size() * sizeof(uint64_t));
+  }
   for (uint32_t i = 0; i < n; ++i) {
     out[i].lo = h[2 * i];
     out[i].hi = h[2 * i + 1];

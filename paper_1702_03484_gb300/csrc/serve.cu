@@ -188,9 +188,9 @@ struct Server {
     bool completes = false;
     for (Query* q : active) completes |= q->status == MAPSQ_OK && q->joined >= q->bgp.size();
     if (completes) {
-      const cudaError_t e = cudaStreamSynchronize(ctx->stream);
-      if (e != cudaSuccess)
-        for (Query* q : active) q->status = q->status == MAPSQ_OK ? MAPSQ_ERR_CUDA : q->status;
+      const int e = read_words(ctx, nullptr, 0, nullptr);
+      if (e != MAPSQ_OK)
+        for (Query* q : active) q->status = q->status == MAPSQ_OK ? e : q->status;
     }
     std::vector<Query*> still;
     for (Query* q : active) {
