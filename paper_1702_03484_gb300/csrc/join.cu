@@ -39,6 +39,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "search.cuh"
 
 namespace mapsq {
 
@@ -71,6 +72,7 @@ constexpr uint64_t kDenseCap = 64;                     // no dense write when a 
 constexpr int kSamples = 2048;                         // sorted key column samples per count CTA (8 KB)
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
 constexpr int kSortedItems = kRowTile / kSortedThreads;
+constexpr int kSearchWays = 4;                         // sorted count: pivots per search round + 1
 constexpr uint32_t kSortedRatio = 4;                   // default: sorted side at least this many times the other's rows
 
 constexpr int kRegionBits = 8;
@@ -706,11 +708,11 @@ __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(con
 
 // Count phase of a sorted join.  The build side's key column is sorted, so a
 // key's group is the run of equal keys: every probe row finds the run's start
-// by a search narrowed first in kSamples evenly spaced samples of the column
-// held in shared memory, then by bisection in global memory between two
-// neighbouring samples, and the run's end by galloping from its start.
-// Counts, group starts and tile-local offsets are then written as in the hash
-// count phase.
+// (first position >= key) and end (first position > key) by two searches,
+// each narrowed first in kSamples evenly spaced samples of the column held in
+// shared memory, then between two neighbouring samples in global memory by
+// K-ary rounds, all four searches of a thread in lockstep.  Counts, group
+// starts and tile-local offsets are then written as in the hash count phase.
 __device__ __forceinline__ uint64_t sample_pos(uint32_t i, uint64_t n) { return uint64_t(i) * n / kSamples; }
 
 
@@ -729,64 +731,46 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
   auto pad = [](int i) { return i + (i >> 5); };
   for (int i = threadIdx.x; i < kSamples; i += kSortedThreads) s_key[i] = __ldg(x + sample_pos(uint32_t(i), nx));
   __syncthreads();
-  // first position >= key: bracket from the samples, then the thread's rows
-  // bisect their brackets in lockstep (their loads overlap)
+  // a key's run is [first position >= key, first position > key): both ends of
+  // every row's run are searched together, bracketed by the samples, then
+  // narrowed K-ary in lockstep (searches 2i and 2i + 1 are row i's ends)
+  constexpr int kS = 2 * kSortedItems;
+  const uint32_t* arr[kS];
+  uint32_t tgt[kS];
+  uint64_t lo[kS], len[kS];
   uint32_t key[kSortedItems];
-  uint64_t lo[kSortedItems], len[kSortedItems];
 #pragma unroll
   for (int it = 0; it < kSortedItems; ++it) {
     const uint64_t row = base + it * kSortedThreads + threadIdx.x;
     key[it] = row < np ? __ldcs(d.pk.c0 + row) : 0u;
-    uint32_t a = 0, b = kSamples;
-    while (a < b) {
-      const uint32_t m = (a + b) >> 1;
-      if (s_key[m] < key[it]) a = m + 1; else b = m;
-    }
-    lo[it] = a ? sample_pos(a - 1, nx) + 1 : 0;
-    len[it] = row < np ? (a < kSamples ? sample_pos(a, nx) : nx) - lo[it] : 0;
-  }
-  for (;;) {
-    bool more = false;
 #pragma unroll
-    for (int it = 0; it < kSortedItems; ++it) more |= len[it] != 0;
-    if (!more) break;
-    uint32_t xm[kSortedItems];
-#pragma unroll
-    for (int it = 0; it < kSortedItems; ++it) xm[it] = len[it] ? __ldg(x + lo[it] + len[it] / 2) : 0u;
-#pragma unroll
-    for (int it = 0; it < kSortedItems; ++it) {
-      if (!len[it]) continue;
-      const uint64_t h = len[it] / 2;
-      if (xm[it] < key[it]) {
-        lo[it] += h + 1;
-        len[it] -= h + 1;
-      } else {
-        len[it] = h;
+    for (int e = 0; e < 2; ++e) {
+      const int q = 2 * it + e;
+      arr[q] = x;
+      tgt[q] = key[it] + uint32_t(e);
+      if (row >= np || (e && key[it] == 0xffffffffu)) {  // nothing to search; no value exceeds the largest key
+        lo[q] = nx;
+        len[q] = 0;
+        continue;
       }
+      uint32_t a = 0, b = kSamples;  // first sample >= the target
+      while (a < b) {
+        const uint32_t m = (a + b) >> 1;
+        if (s_key[m] < tgt[q]) a = m + 1; else b = m;
+      }
+      lo[q] = a ? sample_pos(a - 1, nx) + 1 : 0;
+      len[q] = (a < kSamples ? sample_pos(a, nx) : nx) - lo[q];
     }
   }
+  lower_bounds_kary<kS, kSearchWays>(arr, tgt, lo, len);
 #pragma unroll
   for (int it = 0; it < kSortedItems; ++it) {
     const int loc = it * kSortedThreads + threadIdx.x;
     const uint64_t row = base + loc;
     uint32_t cnt = 0;
     if (row < np) {
-      const uint32_t v = key[it];
-      const uint64_t first_pos = lo[it];
-      if (first_pos < nx && __ldg(x + first_pos) == v) {
-        // end of the run: gallop from its start (short runs stay in one cache line), then bisect
-        uint64_t a = first_pos, step = 1;
-        while (a + step < nx && __ldg(x + a + step) == v) {
-          a += step;
-          step <<= 1;
-        }
-        uint64_t b = min(a + step, nx);  // x[a] == v; x[b] > v or b == nx
-        while (b - a > 1) {
-          const uint64_t m = a + (b - a) / 2;
-          if (__ldg(x + m) == v) a = m; else b = m;
-        }
-        cnt = uint32_t(a + 1 - first_pos);
-      }
+      const uint64_t first_pos = lo[2 * it];
+      cnt = uint32_t(lo[2 * it + 1] - first_pos);
       __stcs(d.pbeg + row, cnt ? uint32_t(first_pos) : 0u);
     }
     s_cnt[pad(loc)] = cnt;

@@ -7,9 +7,8 @@
 // combination of one row from each table.
 //
 // A thread per row of the driving table (the smallest, or the one not
-// sorted) finds its key's run in every other table (binary search, then a
-// galloping search for the run's end) and counts the product of the run
-// lengths; a prefix sum of the counts gives each driving row its output range
+// sorted) finds its key's run in every other table (the run's two ends
+// searched together, K-ary) and counts the product of the run lengths; a prefix sum of the counts gives each driving row its output range
 // (one synchronisation reads the total); the write kernel gives each thread
 // four consecutive output rows, finds their driving row once and decodes each
 // row's position inside its range as a mixed-radix number whose digits index
@@ -21,6 +20,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "search.cuh"
 
 namespace mapsq {
 
@@ -29,6 +29,7 @@ namespace {
 constexpr int kMaxStar = 8;
 constexpr int kStarThreads = 256;
 constexpr int kStarRowsPerThread = 4;
+constexpr int kStarWays = 8;  // pivots per search round + 1
 
 struct StarDesc {
   int k;                                // tables; table 0 drives
@@ -46,41 +47,21 @@ struct StarDesc {
   uint32_t* check;                      // status word of the checked build's bounds checks
 };
 
-__device__ __forceinline__ uint64_t lower_bound_key(const uint32_t* __restrict__ a, uint64_t n, uint32_t x) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint64_t mid = lo + (hi - lo) / 2;
-    if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// End of the run of x that starts at ``first`` (a[first] == x): gallop, then bisect.
-__device__ __forceinline__ uint64_t run_end(const uint32_t* __restrict__ a, uint64_t n, uint64_t first, uint32_t x) {
-  uint64_t at = first, step = 1;
-  while (at + step < n && __ldg(a + at + step) == x) {
-    at += step;
-    step <<= 1;
-  }
-  uint64_t b = min(at + step, n);  // a[at] == x; a[b] > x or b == n
-  while (b - at > 1) {
-    const uint64_t m = at + (b - at) / 2;
-    if (__ldg(a + m) == x) at = m; else b = m;
-  }
-  return at + 1;
-}
-
 __global__ void __launch_bounds__(kStarThreads) star_count_kernel(StarDesc d, uint64_t* __restrict__ status) {
   const uint64_t n0 = d.n[0], stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n0; i += stride) {
     const uint32_t x = __ldg(d.key[0] + i);
     uint64_t c = 1;
     for (int j = 1; j < d.k; ++j) {
-      const uint64_t a = lower_bound_key(d.key[j], d.n[j], x);
-      const uint64_t b = a < d.n[j] && __ldg(d.key[j] + a) == x ? run_end(d.key[j], d.n[j], a, x) : a;
-      d.lo[(j - 1) * n0 + i] = uint32_t(a);
-      d.len[(j - 1) * n0 + i] = uint32_t(b - a);
-      c *= b - a;
+      // the run of x in table j: first position >= x and first position > x, searched together
+      const uint32_t* arr[2] = {d.key[j], d.key[j]};
+      const uint32_t tgt[2] = {x, x + 1u};
+      uint64_t lo[2] = {0, x == 0xffffffffu ? d.n[j] : 0};
+      uint64_t len[2] = {d.n[j], x == 0xffffffffu ? 0 : d.n[j]};
+      lower_bounds_kary<2, kStarWays>(arr, tgt, lo, len);
+      d.lo[(j - 1) * n0 + i] = uint32_t(lo[0]);
+      d.len[(j - 1) * n0 + i] = uint32_t(lo[1] - lo[0]);
+      c *= lo[1] - lo[0];
       if (c == 0) break;
       if (c > 0xffffffffull) {  // one key's product of runs beyond 2^32 rows
         atomicOr(reinterpret_cast<unsigned long long*>(status), 1ull);
@@ -96,13 +77,13 @@ __global__ void __launch_bounds__(kStarThreads) star_write_kernel(StarDesc d) {
   const uint64_t n0 = d.n[0];
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kStarRowsPerThread;
   for (uint64_t t0 = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kStarRowsPerThread; t0 < d.T; t0 += stride) {
-    // the driving row whose output range holds t0: last i with off[i] <= t0
-    uint64_t lo = 0, hi = n0;
-    while (hi - lo > 1) {
-      const uint64_t mid = lo + (hi - lo) / 2;
-      if (d.off[mid] <= t0) lo = mid; else hi = mid;
-    }
-    uint64_t i = lo;
+    // the driving row whose output range holds t0: last i with off[i] <= t0,
+    // one before the first i with off[i] > t0 (off[0] = 0 <= t0, off[n0] = T > t0)
+    const uint64_t* arr[1] = {d.off};
+    const uint64_t tgt[1] = {t0 + 1};
+    uint64_t lo[1] = {1}, len[1] = {n0 - 1};
+    lower_bounds_kary<1, kStarWays>(arr, tgt, lo, len);
+    uint64_t i = lo[0] - 1;
     const uint64_t tend = min(t0 + kStarRowsPerThread, d.T);
     for (uint64_t t = t0; t < tend; ++t) {
       while (d.off[i + 1] <= t) ++i;  // rows without output are skipped
