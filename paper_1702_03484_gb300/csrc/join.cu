@@ -73,6 +73,7 @@ constexpr int kSamples = 2048;                         // sorted key column samp
 constexpr int kSortedThreads = 1024;                   // threads of the sorted count (two rows each)
 constexpr int kSortedItems = kRowTile / kSortedThreads;
 constexpr int kSearchWays = 4;                         // sorted count: pivots per search round + 1
+constexpr uint64_t kKaryMaxItems = 152;                // sorted count launches of up to this many CTAs search K-ary
 constexpr uint32_t kSortedRatio = 4;                   // default: sorted side at least this many times the other's rows
 
 constexpr int kRegionBits = 8;
@@ -707,19 +708,22 @@ __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(con
 }
 
 // Count phase of a sorted join.  The build side's key column is sorted, so a
-// key's group is the run of equal keys: every probe row finds the run's start
-// (first position >= key) and end (first position > key) by two searches,
-// each narrowed first in kSamples evenly spaced samples of the column held in
-// shared memory, then between two neighbouring samples in global memory by
-// K-ary rounds, all four searches of a thread in lockstep.  Counts, group
-// starts and tile-local offsets are then written as in the hash count phase.
+// key's group is the run of equal keys.  Every probe row's search is narrowed
+// first in kSamples evenly spaced samples of the column held in shared
+// memory, then between two neighbouring samples in global memory.  A launch of
+// few CTAs (bound by the latency of its dependent loads) searches the run's
+// start (first position >= key) and end (first position > key) together in
+// K-ary rounds, all searches of a thread in lockstep; a larger launch (bound by
+// its loads' throughput) bisects for the start and gallops for the end, fewer
+// loads per row.  Counts, group starts and tile-local offsets are then written
+// as in the hash count phase.
 __device__ __forceinline__ uint64_t sample_pos(uint32_t i, uint64_t n) { return uint64_t(i) * n / kSamples; }
 
 
 __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const JoinDesc* __restrict__ jd,
                                                                      const uint64_t* first, uint32_t k,
                                                                      uint32_t* __restrict__ status,
-                                                                     uint64_t* __restrict__ totals) {
+                                                                     uint64_t* __restrict__ totals, bool kary) {
   __shared__ uint32_t s_key[kSamples];
   __shared__ uint32_t s_cnt[kRowTile + kRowTile / 32];
   __shared__ uint64_t s_warp[kSortedThreads / 32];
@@ -731,47 +735,98 @@ __global__ void __launch_bounds__(kSortedThreads) sorted_count_kernel(const Join
   auto pad = [](int i) { return i + (i >> 5); };
   for (int i = threadIdx.x; i < kSamples; i += kSortedThreads) s_key[i] = __ldg(x + sample_pos(uint32_t(i), nx));
   __syncthreads();
-  // a key's run is [first position >= key, first position > key): both ends of
-  // every row's run are searched together, bracketed by the samples, then
-  // narrowed K-ary in lockstep (searches 2i and 2i + 1 are row i's ends)
-  constexpr int kS = 2 * kSortedItems;
-  const uint32_t* arr[kS];
-  uint32_t tgt[kS];
-  uint64_t lo[kS], len[kS];
+  // first position >= t, bracketed by the samples: [lo, lo + len]
+  auto bracket = [&](uint32_t t, uint64_t* lo, uint64_t* len) {
+    uint32_t a = 0, b = kSamples;  // first sample >= t
+    while (a < b) {
+      const uint32_t m = (a + b) >> 1;
+      if (s_key[m] < t) a = m + 1; else b = m;
+    }
+    *lo = a ? sample_pos(a - 1, nx) + 1 : 0;
+    *len = (a < kSamples ? sample_pos(a, nx) : nx) - *lo;
+  };
   uint32_t key[kSortedItems];
+  uint64_t first_pos[kSortedItems], run_len[kSortedItems];
 #pragma unroll
   for (int it = 0; it < kSortedItems; ++it) {
     const uint64_t row = base + it * kSortedThreads + threadIdx.x;
     key[it] = row < np ? __ldcs(d.pk.c0 + row) : 0u;
+  }
+  if (kary) {
+    // latency-bound launch: a key's run is [first position >= key, first
+    // position > key), both ends of every row's run searched together, K-ary
+    // rounds in lockstep (searches 2i and 2i + 1 are row i's ends)
+    constexpr int kS = 2 * kSortedItems;
+    const uint32_t* arr[kS];
+    uint32_t tgt[kS];
+    uint64_t lo[kS], len[kS];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int q = 2 * it + e;
-      arr[q] = x;
-      tgt[q] = key[it] + uint32_t(e);
-      if (row >= np || (e && key[it] == 0xffffffffu)) {  // nothing to search; no value exceeds the largest key
-        lo[q] = nx;
-        len[q] = 0;
-        continue;
+    for (int it = 0; it < kSortedItems; ++it) {
+      const uint64_t row = base + it * kSortedThreads + threadIdx.x;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int q = 2 * it + e;
+        arr[q] = x;
+        tgt[q] = key[it] + uint32_t(e);
+        if (row >= np || (e && key[it] == 0xffffffffu)) {  // nothing to search; no value exceeds the largest key
+          lo[q] = nx;
+          len[q] = 0;
+        } else {
+          bracket(tgt[q], &lo[q], &len[q]);
+        }
       }
-      uint32_t a = 0, b = kSamples;  // first sample >= the target
-      while (a < b) {
-        const uint32_t m = (a + b) >> 1;
-        if (s_key[m] < tgt[q]) a = m + 1; else b = m;
+    }
+    lower_bounds_kary<kS, kSearchWays>(arr, tgt, lo, len);
+#pragma unroll
+    for (int it = 0; it < kSortedItems; ++it) {
+      first_pos[it] = lo[2 * it];
+      run_len[it] = lo[2 * it + 1] - lo[2 * it];
+    }
+  } else {
+    // throughput-bound launch (fewer loads per row): the run's start by
+    // bisection in lockstep, its end by galloping from the start (short runs
+    // stay in one cache line), then bisecting
+    const uint32_t* arr[kSortedItems];
+    uint64_t len[kSortedItems];
+#pragma unroll
+    for (int it = 0; it < kSortedItems; ++it) {
+      arr[it] = x;
+      const uint64_t row = base + it * kSortedThreads + threadIdx.x;
+      if (row < np) {
+        bracket(key[it], &first_pos[it], &len[it]);
+      } else {
+        first_pos[it] = nx;
+        len[it] = 0;
       }
-      lo[q] = a ? sample_pos(a - 1, nx) + 1 : 0;
-      len[q] = (a < kSamples ? sample_pos(a, nx) : nx) - lo[q];
+    }
+    lower_bounds_kary<kSortedItems, 2>(arr, key, first_pos, len);
+#pragma unroll
+    for (int it = 0; it < kSortedItems; ++it) {
+      const uint32_t v = key[it];
+      run_len[it] = 0;
+      if (first_pos[it] < nx && __ldg(x + first_pos[it]) == v) {
+        uint64_t a = first_pos[it], step = 1;
+        while (a + step < nx && __ldg(x + a + step) == v) {
+          a += step;
+          step <<= 1;
+        }
+        uint64_t b = min(a + step, nx);  // x[a] == v; x[b] > v or b == nx
+        while (b - a > 1) {
+          const uint64_t m = a + (b - a) / 2;
+          if (__ldg(x + m) == v) a = m; else b = m;
+        }
+        run_len[it] = a + 1 - first_pos[it];
+      }
     }
   }
-  lower_bounds_kary<kS, kSearchWays>(arr, tgt, lo, len);
 #pragma unroll
   for (int it = 0; it < kSortedItems; ++it) {
     const int loc = it * kSortedThreads + threadIdx.x;
     const uint64_t row = base + loc;
     uint32_t cnt = 0;
     if (row < np) {
-      const uint64_t first_pos = lo[2 * it];
-      cnt = uint32_t(lo[2 * it + 1] - first_pos);
-      __stcs(d.pbeg + row, cnt ? uint32_t(first_pos) : 0u);
+      cnt = uint32_t(run_len[it]);
+      __stcs(d.pbeg + row, cnt ? uint32_t(first_pos[it]) : 0u);
     }
     s_cnt[pad(loc)] = cnt;
     const unsigned nz = __ballot_sync(0xffffffffu, cnt != 0);  // the warp's 32 consecutive rows
@@ -1615,8 +1670,8 @@ struct BatchJoin {
       bytes = 0;
       for (auto& pl : plans) bytes += pl.sorted ? 4.0 * pl.np : 0;
       const int r = rec(K_SORTED_COUNT);
-      sorted_count_kernel<<<unsigned(items(PH_SORTED)), kSortedThreads, 0, stream>>>(d_descs, phase_first(PH_SORTED),
-                                                                                     k, status, d_tail + 2);
+      sorted_count_kernel<<<unsigned(items(PH_SORTED)), kSortedThreads, 0, stream>>>(
+          d_descs, phase_first(PH_SORTED), k, status, d_tail + 2, items(PH_SORTED) <= kKaryMaxItems);
       launched();
       done(r, bytes);
     }

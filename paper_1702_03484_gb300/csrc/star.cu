@@ -8,8 +8,11 @@
 //
 // A thread per row of the driving table (the smallest, or the one not
 // sorted) finds its key's run in every other table (the run's two ends
-// searched together, K-ary) and counts the product of the run lengths; a prefix sum of the counts gives each driving row its output range
-// (one synchronisation reads the total); the write kernel gives each thread
+// searched together: K-ary rounds in a launch of few CTAs, where the latency
+// of dependent loads decides, bisection in a larger one, where their number
+// does) and counts the product of the run lengths; a prefix sum of the counts
+// gives each driving row its output range (one synchronisation reads the
+// total); the write kernel gives each thread
 // four consecutive output rows, finds their driving row once and decodes each
 // row's position inside its range as a mixed-radix number whose digits index
 // the other tables' runs (the last table varies fastest).  Output columns: the
@@ -29,7 +32,8 @@ namespace {
 constexpr int kMaxStar = 8;
 constexpr int kStarThreads = 256;
 constexpr int kStarRowsPerThread = 4;
-constexpr int kStarWays = 8;  // pivots per search round + 1
+constexpr int kStarWays = 8;               // pivots per search round + 1 in a latency-bound launch
+constexpr unsigned kStarKaryMaxBlocks = 152;  // launches of up to this many CTAs search K-ary, larger ones bisect
 
 struct StarDesc {
   int k;                                // tables; table 0 drives
@@ -47,6 +51,7 @@ struct StarDesc {
   uint32_t* check;                      // status word of the checked build's bounds checks
 };
 
+template <int W>
 __global__ void __launch_bounds__(kStarThreads) star_count_kernel(StarDesc d, uint64_t* __restrict__ status) {
   const uint64_t n0 = d.n[0], stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n0; i += stride) {
@@ -58,7 +63,7 @@ __global__ void __launch_bounds__(kStarThreads) star_count_kernel(StarDesc d, ui
       const uint32_t tgt[2] = {x, x + 1u};
       uint64_t lo[2] = {0, x == 0xffffffffu ? d.n[j] : 0};
       uint64_t len[2] = {d.n[j], x == 0xffffffffu ? 0 : d.n[j]};
-      lower_bounds_kary<2, kStarWays>(arr, tgt, lo, len);
+      lower_bounds_kary<2, W>(arr, tgt, lo, len);
       d.lo[(j - 1) * n0 + i] = uint32_t(lo[0]);
       d.len[(j - 1) * n0 + i] = uint32_t(lo[1] - lo[0]);
       c *= lo[1] - lo[0];
@@ -73,6 +78,7 @@ __global__ void __launch_bounds__(kStarThreads) star_count_kernel(StarDesc d, ui
   }
 }
 
+template <int W>
 __global__ void __launch_bounds__(kStarThreads) star_write_kernel(StarDesc d) {
   const uint64_t n0 = d.n[0];
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kStarRowsPerThread;
@@ -82,7 +88,7 @@ __global__ void __launch_bounds__(kStarThreads) star_write_kernel(StarDesc d) {
     const uint64_t* arr[1] = {d.off};
     const uint64_t tgt[1] = {t0 + 1};
     uint64_t lo[1] = {1}, len[1] = {n0 - 1};
-    lower_bounds_kary<1, kStarWays>(arr, tgt, lo, len);
+    lower_bounds_kary<1, W>(arr, tgt, lo, len);
     uint64_t i = lo[0] - 1;
     const uint64_t tend = min(t0 + kStarRowsPerThread, d.T);
     for (uint64_t t = t0; t < tend; ++t) {
@@ -213,7 +219,11 @@ int join_star(Ctx* ctx, uint32_t k, const mapsq_table* const* tabs, int32_t key_
   d.off = off;
   MQ_CUDA(cudaMemsetAsync(off + n0 + 1, 0, sizeof(uint64_t), ctx->stream));
   int rec = prof_begin(ctx, K_STAR_COUNT);
-  star_count_kernel<<<star_grid(n0, 1), kStarThreads, 0, ctx->stream>>>(d, off + n0 + 1);
+  const unsigned gc = star_grid(n0, 1);
+  if (gc <= kStarKaryMaxBlocks)
+    star_count_kernel<kStarWays><<<gc, kStarThreads, 0, ctx->stream>>>(d, off + n0 + 1);
+  else
+    star_count_kernel<2><<<gc, kStarThreads, 0, ctx->stream>>>(d, off + n0 + 1);
   ++ctx->launches;
   prof_end(ctx, rec, 4.0 * n0);
   MQ_CUDA(cudaGetLastError());
@@ -229,7 +239,11 @@ int join_star(Ctx* ctx, uint32_t k, const mapsq_table* const* tabs, int32_t key_
     double bytes = 4.0 * double(d.T) * ncols;
     for (uint32_t s = 0; s < k; ++s) bytes += 4.0 * double(d.n[s]);
     rec = prof_begin(ctx, K_STAR_WRITE);
-    star_write_kernel<<<star_grid(d.T, kStarRowsPerThread), kStarThreads, 0, ctx->stream>>>(d);
+    const unsigned gw = star_grid(d.T, kStarRowsPerThread);
+    if (gw <= kStarKaryMaxBlocks)
+      star_write_kernel<kStarWays><<<gw, kStarThreads, 0, ctx->stream>>>(d);
+    else
+      star_write_kernel<2><<<gw, kStarThreads, 0, ctx->stream>>>(d);
     ++ctx->launches;
     prof_end(ctx, rec, bytes);
     const cudaError_t e = cudaGetLastError();
