@@ -333,6 +333,25 @@ def test_sorted_build_side(ctx):
         ctx.set_profiling(False)
 
 
+def test_sorted_count_both_search_modes(ctx):
+    """A probe side of a few tiles (the count searches K-ary, both ends of a
+    run together) and one of more than 152 tiles (bisection for the start,
+    galloping for the end) give the oracle's rows, with long runs, keys below
+    and above the sorted column's range and the largest id."""
+    r = gen.Rng(78)
+    X = _sorted_table(r, 2_000_000, [0, 4], 0, 1 << 20)
+    X.cols[0][:2000] = 0                     # a long run at the start
+    X.cols[0][-700:] = 0xFFFFFFFF            # and at the end
+    X.cols[0][1_000_000:1_050_000] = X.cols[0][1_000_000]  # one in the middle
+    X.cols[0].sort()
+    for ny in (5_000, 700_000):
+        Y = gen.Table([0, 7], [r.below(ny, (1 << 20) + 50).astype(np.uint32), r.u32(ny)])
+        Y.cols[0][:4] = [0, 0xFFFFFFFF, 0xFFFFFFFE, int(X.cols[0][1_000_000])]
+        out, used = _sorted_join(ctx, X, Y, False, algorithm=2)
+        assert_same_multiset(out, oracle.join_mapreduce(Y, X), f"probe rows {ny}")
+        out.free()
+
+
 def test_autotune_sets_ratio_and_joins_stay_exact():
     from paper_1702_03484_gb300 import Context, MapsqError
     with Context(device=0) as c:

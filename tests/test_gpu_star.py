@@ -82,6 +82,17 @@ def test_hot_key_large_product_and_key_only_tables(ctx):
     _check(ctx, only, what="key-only tables")
 
 
+def test_large_stars_search_by_bisection(ctx):
+    """Driving tables of more than 152 CTAs' rows (the count and write bisect
+    instead of searching K-ary) give the oracle's rows."""
+    r = gen.Rng(54)
+    for k in (2, 4):
+        tabs = [gen.Table([0, j + 1], [r.below(60_000 + 7000 * j, 50_000).astype(np.uint32),
+                                       r.u32(60_000 + 7000 * j)]) for j in range(k)]
+        tabs[1].cols[0][:3] = [0, 0xFFFFFFFF, 0xFFFFFFFF]
+        assert _check(ctx, tabs, what=f"large star k {k}") > 0
+
+
 def test_empty_table_and_errors(ctx):
     from paper_1702_03484_gb300 import mapsq
     from paper_1702_03484_gb300.mapsq import MapsqError
