@@ -14,7 +14,7 @@ const char* const kKernelNames[K_COUNT_KERNELS] = {
     "scan_ranges",           "scan_emit",           "scan_filter", "prefix_sum",
     "hash_insert",           "hash_scatter",        "probe_count", "join_write",
     "cross_write",           "copy",        "hll_sketch",  "write_partition", "sorted_count", "dense_write",
-    "partition_build", "star_count", "star_write"};
+    "partition_build", "star_count", "star_write", "fused_join"};
 
 int set_error(Ctx* ctx, int code, const char* fmt, ...) {
   if (ctx) {

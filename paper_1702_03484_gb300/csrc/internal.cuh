@@ -53,6 +53,7 @@ enum KernelId {
   K_PARTITION_BUILD,
   K_STAR_COUNT,
   K_STAR_WRITE,
+  K_FUSED_JOIN,
   K_COUNT_KERNELS
 };
 

@@ -39,6 +39,7 @@
 #include <mutex>
 
 #include "internal.cuh"
+#include "lookback.cuh"
 #include "search.cuh"
 
 namespace mapsq {
@@ -57,6 +58,8 @@ constexpr int kWriteBlocks = 4;                        // write CTAs per SM (reg
 constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
 constexpr int kProbeIn = 2;                            // probe rows in flight per thread
 constexpr int kProbeBlocks = 5;                        // probe CTAs per SM (register budget)
+constexpr int kFusedBlocks = 6;                        // one-pass dense join CTAs per SM (register budget)
+constexpr uint64_t kFusedMinProbe = uint64_t(1) << 20;  // probe sides from which a dense join may take one pass
 constexpr int kEarlyTiles = 64;                        // joins of up to this many write tiles are partitioned by the count scan
 constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
 constexpr int kWriteSmem = int(sizeof(uint32_t)) * (2 * kStageRows + 1 + 2 * kMapWords);  // write kernel's dynamic shared memory
@@ -485,20 +488,40 @@ __device__ __forceinline__ void single_tile_finish(const JoinDesc& d, uint64_t t
 }
 
 // Slot tiles: the group starts inside each tile of kRowTile slots (written into
-// group[].y) and the tile's total.
+// group[].y) and the tile's total; per join, the largest group (groups[j])
+// and the number of groups (groups[k + j]).
 __global__ void __launch_bounds__(kThreads) slot_scan_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
-                                                            uint32_t k) {
+                                                            uint32_t k, uint64_t* __restrict__ groups) {
   __shared__ uint64_t s_warp[kThreads / 32];
   const uint32_t j = item_join(first, k, blockIdx.x);
   const JoinDesc& d = jd[j];
   const uint64_t base = (blockIdx.x - first[j]) * kRowTile, n = uint64_t(d.t.M) + 1;
   uint32_t c[kRowItems];
   uint64_t sum = 0;
+  uint32_t most = 0, nonzero = 0;
 #pragma unroll
   for (int it = 0; it < kRowItems; ++it) {
     const uint64_t s = base + uint64_t(threadIdx.x) * kRowItems + it;
     c[it] = s < n ? group_of(d.t, uint32_t(s))->x : 0u;
     sum += c[it];
+    most = max(most, c[it]);
+    nonzero += c[it] != 0;
+  }
+  __shared__ uint32_t s_most[kThreads / 32], s_nonzero[kThreads / 32];
+  most = __reduce_max_sync(0xffffffffu, most);
+  nonzero = __reduce_add_sync(0xffffffffu, nonzero);
+  if ((threadIdx.x & 31) == 0) {
+    s_most[threadIdx.x >> 5] = most;
+    s_nonzero[threadIdx.x >> 5] = nonzero;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // one atomic of each kind per CTA
+    for (int w = 1; w < kThreads / 32; ++w) {
+      most = max(most, s_most[w]);
+      nonzero += s_nonzero[w];
+    }
+    if (most) atomicMax(reinterpret_cast<unsigned long long*>(groups + j), (unsigned long long)most);
+    if (nonzero) atomicAdd(reinterpret_cast<unsigned long long*>(groups + k + j), (unsigned long long)nonzero);
   }
   uint64_t total;
   uint64_t run = block_scan(sum, s_warp, &total);
@@ -1166,6 +1189,32 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
   }
 }
 
+// Output rows [o, o + c) of probe row i, whose key group starts at build row
+// g: every column in chunks of four output rows, one 16-byte store when the
+// chunk is whole and aligned.
+__device__ __forceinline__ void write_dense_row(const JoinDesc& d, int ncols, uint32_t bstride, uint64_t i, uint64_t o,
+                                                uint32_t c, uint32_t g) {
+  for (int col = 0; col < ncols; ++col) {
+    uint32_t* __restrict__ dst = d.out[col] + o;
+    const uint32_t* __restrict__ src = d.src[col];
+    const bool from_build = (d.from_build >> col) & 1u;
+    const uint32_t pv = from_build ? 0u : __ldg(src + i);
+    for (uint32_t j0 = 0; j0 < c; j0 += kVec) {
+      uint32_t x[kVec];
+#pragma unroll
+      for (int j = 0; j < kVec; ++j)
+        x[j] = !from_build ? pv : j0 + j < c ? __ldg(src + uint64_t(g + j0 + j) * bstride) : 0u;
+      if (j0 + kVec <= c && !((o + j0) & (kVec - 1))) {
+        __stcs(reinterpret_cast<uint4*>(dst + j0), make_uint4(x[0], x[1], x[2], x[3]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < kVec; ++j)
+          if (j0 + j < c) __stcs(dst + j0 + j, x[j]);
+      }
+    }
+  }
+}
+
 // Write phase of a join whose probe rows have few matches (on average at most
 // the autotuned crossover, none more than kDenseCap): a thread per probe row
 // writes that row's output rows.  Consecutive threads
@@ -1192,26 +1241,110 @@ __global__ void __launch_bounds__(kThreads) dense_write_kernel(const JoinDesc* _
     if (!c) continue;
     const uint32_t g = d.pbeg[i];
     if (!MQ_IN_BOUNDS(e <= d.T && uint64_t(g) + c <= d.nb, d.check)) continue;
-    for (int col = 0; col < ncols; ++col) {
-      uint32_t* __restrict__ dst = d.out[col] + o;
-      const uint32_t* __restrict__ src = d.src[col];
-      const bool from_build = (d.from_build >> col) & 1u;
-      const uint32_t pv = from_build ? 0u : __ldg(src + i);
-      // chunks of four output rows: one 16-byte store when whole and aligned
-      for (uint32_t j0 = 0; j0 < c; j0 += kVec) {
-        uint32_t x[kVec];
+    write_dense_row(d, ncols, bstride, i, o, c, g);
+  }
+}
+
+// One pass for a dense hash join whose output size is bounded before the
+// count: no probe row has more matches than the largest key group of the
+// build side, so capacity ``cap`` = probe rows x that group size holds the
+// output.  Each CTA takes the next probe tile by an atomic ticket, looks its
+// rows up as the count phase does (keeping each row's count and group start
+// in shared memory), scans the counts, learns the tile's output offset by
+// decoupled look-back over the tiles before it (a tile publishes its sum as
+// soon as its lookups end, before it writes), then writes its rows' output as
+// the dense write does.  The probe keys are read once, and no group start or
+// offset goes through global memory.  The last tile writes the row count.
+// Status bits: 2 a look-back wait gave up, 4 a tile of 2^32 or more rows,
+// 8 an output range beyond the capacity or a group beyond the build side.
+__global__ void __launch_bounds__(kThreads, kFusedBlocks) fused_dense_kernel(const JoinDesc* __restrict__ jd,
+                                                                          uint64_t* __restrict__ scratch,
+                                                                          uint32_t* __restrict__ status,
+                                                                          uint32_t spin_limit, uint64_t cap,
+                                                                          uint64_t* __restrict__ total) {
+  __shared__ uint32_t s_cnt[kRowTile + kRowTile / 32];  // counts, then tile-local offsets
+  __shared__ uint32_t s_beg[kRowTile];
+  __shared__ uint64_t s_warp[kThreads / 32];
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_prefix;
+  const JoinDesc& d = jd[0];
+  const HashTable t = d.t;
+  auto pad = [](int i) { return i + (i >> 5); };
+  if (threadIdx.x == 0) s_tile = uint32_t(atomicAdd(reinterpret_cast<unsigned long long*>(scratch), 1ull));
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = uint64_t(tile) * kRowTile, np = d.np;
+  if (base >= np) return;  // the same for the whole block
+  // lookups, kProbeIn rows in flight per thread (keys loaded as they are
+  // needed: the registers go to more CTAs per SM)
 #pragma unroll
-        for (int j = 0; j < kVec; ++j)
-          x[j] = !from_build ? pv : j0 + j < c ? __ldg(src + uint64_t(g + j0 + j) * bstride) : 0u;
-        if (j0 + kVec <= c && !((o + j0) & (kVec - 1))) {
-          __stcs(reinterpret_cast<uint4*>(dst + j0), make_uint4(x[0], x[1], x[2], x[3]));
-        } else {
+  for (int h0 = 0; h0 < kRowItems; h0 += kProbeIn) {
+    uint64_t key[kProbeIn];
+    uint32_t b[kProbeIn], sl[kProbeIn];
+    ulonglong2 k01[kProbeIn], k23[kProbeIn];
 #pragma unroll
-          for (int j = 0; j < kVec; ++j)
-            if (j0 + j < c) __stcs(dst + j0 + j, x[j]);
-        }
-      }
+    for (int q = 0; q < kProbeIn; ++q) {
+      const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+      key[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
     }
+#pragma unroll
+    for (int q = 0; q < kProbeIn; ++q)
+      if (key[q] != kEmptyKey) load_bucket(t, key[q], &b[q], &k01[q], &k23[q]);
+#pragma unroll
+    for (int q = 0; q < kProbeIn; ++q) {
+      const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+      sl[q] = row < np ? find_slot(t, key[q], b[q], k01[q], k23[q]) : kNoSlot;
+    }
+#pragma unroll
+    for (int q = 0; q < kProbeIn; ++q) {
+      const int loc = (h0 + q) * kThreads + threadIdx.x;
+      const uint2 g = sl[q] != kNoSlot ? *group_of(t, sl[q]) : make_uint2(0u, 0u);
+      s_beg[loc] = g.x ? group_begin(t, sl[q], g.y) : 0u;
+      s_cnt[pad(loc)] = g.x;
+    }
+  }
+  __syncthreads();
+  uint32_t v[kRowItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    v[q] = s_cnt[pad(threadIdx.x * kRowItems + q)];
+    sum += v[q];
+  }
+  uint64_t tile_sum;
+  uint64_t run = block_scan(sum, s_warp, &tile_sum);
+  if (threadIdx.x < 32) {
+    const uint64_t p = lb_tile_prefix(scratch + 1, tile, tile_sum, status, spin_limit);
+    if (threadIdx.x == 0) s_prefix = p;
+  }
+#pragma unroll
+  for (int q = 0; q < kRowItems; ++q) {
+    s_cnt[pad(threadIdx.x * kRowItems + q)] = uint32_t(run);
+    run += v[q];
+  }
+  __syncthreads();
+  const uint64_t prefix = s_prefix;
+  if (threadIdx.x == 0) {
+    if (base + kRowTile >= np) *total = prefix + tile_sum;
+    if (tile_sum > 0xffffffffull) atomicOr(status, 4u);
+  }
+  const int ncols = d.ncols;
+  const uint32_t bstride = d.bstride;
+#pragma unroll kDenseUnroll
+  for (int it = 0; it < kRowItems; ++it) {
+    const int loc = it * kThreads + threadIdx.x;
+    const uint64_t i = base + loc;
+    if (i >= np) break;  // later rows of this thread are past the end too
+    const uint32_t off = s_cnt[pad(loc)];
+    const uint32_t c = uint32_t((loc + 1 < kRowTile ? uint64_t(s_cnt[pad(loc + 1)]) : tile_sum) - off);
+    if (!c) continue;
+    const uint64_t o = prefix + off;
+    const uint32_t g = s_beg[loc];
+    if (o + c > cap || uint64_t(g) + c > d.nb) {
+      atomicOr(status, 8u);
+      continue;
+    }
+    write_dense_row(d, ncols, bstride, i, o, c, g);
   }
 }
 
@@ -1330,6 +1463,8 @@ struct BatchJoin {
   uint32_t sorted_ratio = kSortedRatio;
   uint64_t part_min_build = kHllMinBuild;  // build rows from which a hash build is partitioned first
   uint64_t dense_max = kDenseMax;          // largest mean matches per probe row for the dense write
+  bool allow_fused = false;                // a single large dense hash join may take one pass (join_batch)
+  bool fused = false;                      // it does: plans[0].T is the output's capacity until write()
 
   // The context's autotuned choices (hash vs sorted, partitioned build, dense write).
   void tune_from(const Ctx* c) {
@@ -1356,6 +1491,7 @@ struct BatchJoin {
   // Reads ``words`` 64-bit words into host[0, words) (synchronises the stream).
   int readback(const void* dptr, size_t words) {
     host.assign(words, 0);
+    if (ctx && words <= kReadWords) return read_words(ctx, dptr, words, host.data());
     MQ_TRY(cuda(cudaMemcpyAsync(host.data(), dptr, words * 8, cudaMemcpyDeviceToHost, stream), "readback"));
     return cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
   }
@@ -1483,10 +1619,12 @@ struct BatchJoin {
 
   // Descriptors, item offsets and a zeroed tail go up together, in one copy.
   // The tail holds the status word, the write phase's work counter, the joins'
-  // row counts and their largest match counts per probe row, so that each
-  // upload resets them and one copy reads back all.
+  // row counts, their largest match counts per probe row, their largest key
+  // groups and their numbers of groups, so that each upload resets them and
+  // one copy reads back all.
   uint64_t* d_tail = nullptr;
-  size_t blob_bytes() const { return sizeof(JoinDesc) * k + sizeof(uint64_t) * first.size() + sizeof(uint64_t) * (2 + 2 * k); }
+  size_t tail_words() const { return 2 + 4 * size_t(k); }
+  size_t blob_bytes() const { return sizeof(JoinDesc) * k + sizeof(uint64_t) * first.size() + sizeof(uint64_t) * tail_words(); }
   int ensure_blob() {
     if (d_descs) return MAPSQ_OK;
     const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size();
@@ -1499,7 +1637,7 @@ struct BatchJoin {
     return MAPSQ_OK;
   }
   int upload_descs() {
-    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size(), tb = sizeof(uint64_t) * (2 + 2 * k);
+    const size_t db = sizeof(JoinDesc) * k, fb = sizeof(uint64_t) * first.size(), tb = sizeof(uint64_t) * tail_words();
     MQ_TRY(ensure_blob());
     blob_host.assign(db + fb + tb, 0);
     memcpy(blob_host.data(), descs.data(), db);
@@ -1627,7 +1765,8 @@ struct BatchJoin {
     return cuda(cudaGetLastError(), "partition_kernel");
   }
 
-  int count_phases() {
+  // Build phases of the hash joins: partition, insert, group starts, scatter.
+  int build_phases() {
     MQ_TRY(upload_descs());
     MQ_TRY(partition_phase());
     double bytes = 0;
@@ -1643,7 +1782,8 @@ struct BatchJoin {
       bytes = 0;
       for (auto& pl : plans) bytes += pl.hash ? 16.0 * (pl.M + 1) : 0;
       const int r = rec(K_PREFIX_SUM);
-      slot_scan_kernel<<<unsigned(items(PH_SLOTS)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SLOTS), k);
+      slot_scan_kernel<<<unsigned(items(PH_SLOTS)), kThreads, 0, stream>>>(d_descs, phase_first(PH_SLOTS), k,
+                                                                          d_tail + 2 + 2 * size_t(k));
       launched();
       tiles_scan_kernel<<<k, 1024, 0, stream>>>(d_descs, k, 0, nullptr);
       launched();
@@ -1657,8 +1797,13 @@ struct BatchJoin {
       launched();
       done(r, bytes);
     }
+    return cuda(cudaGetLastError(), "build phases");
+  }
+
+  // Count phases: every probe row's matches, then the tile offsets.
+  int probe_phases() {
+    double bytes = 0;
     if (items(PH_COUNT)) {
-      bytes = 0;
       for (auto& pl : plans) bytes += pl.hash ? 4.0 * pl.lay.nkey * pl.np : 0;
       const int r = rec(K_PROBE_COUNT);
       probe_count_kernel<<<unsigned(items(PH_COUNT)), kThreads, 0, stream>>>(d_descs, phase_first(PH_COUNT), k,
@@ -1685,6 +1830,43 @@ struct BatchJoin {
     return cuda(cudaGetLastError(), "count phases");
   }
 
+  int count_phases() {
+    MQ_TRY(build_phases());
+    return probe_phases();
+  }
+
+  // Reads the first ``words`` words of the tail into host[] (and the context's
+  // status word: an earlier call's write phase may have set it).
+  int read_tail(size_t words) {
+    host.assign(words, 0);
+    if (ctx && words <= kReadWords) return read_words(ctx, d_tail, words, host.data());
+    // through the context's pinned buffer when it is large enough (a pageable copy is slower)
+    // (words 0-63 of it are left to read_u64 and the status word)
+    uint64_t* dst = ctx && words + 64 <= kPinnedWords ? ctx->h_pinned + 64 : host.data();
+    MQ_TRY(cuda(cudaMemcpyAsync(dst, d_tail, words * 8, cudaMemcpyDeviceToHost, stream), "readback"));
+    if (ctx)
+      MQ_TRY(cuda(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                  stream), "readback"));
+    MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
+    if (dst != host.data()) memcpy(host.data(), dst, words * 8);
+    return ctx ? check_status(ctx) : MAPSQ_OK;
+  }
+
+  // A single dense hash join with a large probe side may take one pass
+  // (fused_dense_kernel) if its build groups are even enough that probe rows x
+  // the largest group bounds the output closely: that bound is allocated.
+  bool fused_candidate() const {
+    return allow_fused && ctx && k == 1 && take[0] && plans[0].hash && plans[0].np >= kFusedMinProbe &&
+           plans[0].lay.ncols > 0;
+  }
+  bool fused_fits(uint64_t maxg, uint64_t ngroups) const {
+    const JoinPlan& pl = plans[0];
+    if (maxg == 0 || maxg > dense_max || maxg > kDenseCap || maxg * ngroups > 2 * pl.nb) return false;
+    const uint64_t cap = pl.np * maxg;
+    const uint64_t bytes = ((cap + 63) & ~uint64_t(63)) * uint64_t(pl.lay.ncols) * 4;
+    return !ctx->budget || ctx->in_use + bytes <= ctx->budget / 2;
+  }
+
   int count() {
     MQ_TRY(size_tables());
     MQ_TRY(ensure_blob());
@@ -1694,24 +1876,31 @@ struct BatchJoin {
     for (int attempt = 0;; ++attempt) {
       if (attempt) mem->rewind(mark);
       MQ_TRY(allocate());
-      MQ_TRY(count_phases());  // its upload zeroes the status word
-      // one read: status word, work counter, row counts and largest counts
-      // (and the context's status word: an earlier call's write phase may have set it)
-      host.assign(2 + 2 * size_t(k), 0);
-      if (ctx && host.size() <= kReadWords) {
-        MQ_TRY(read_words(ctx, d_tail, host.size(), host.data()));
+      const bool cand = fused_candidate();
+      if (cand) {
+        // the build first: its largest group and number of groups decide
+        MQ_TRY(build_phases());
+        MQ_TRY(read_tail(tail_words()));
+        const uint32_t st = uint32_t(host[0]);
+        if (st & 1u) {
+          if (attempt > 0) return fail(MAPSQ_ERR_CUDA, "hash table full");
+          plans[0].M = (std::max<uint64_t>(1024, 2 * plans[0].nb) + kBucket - 1) / kBucket * kBucket;
+          continue;
+        }
+        if (st) return fail(MAPSQ_ERR_CUDA, "device status word set");
+        const uint64_t maxg = host[2 + 2 * size_t(k)], ngroups = host[2 + 3 * size_t(k)];
+        if (fused_fits(maxg, ngroups)) {
+          fused = true;
+          plans[0].maxc = maxg;
+          plans[0].T = descs[0].T = plans[0].np * maxg;  // the capacity; write() learns the row count
+          return MAPSQ_OK;
+        }
+        MQ_TRY(probe_phases());
       } else {
-        // through the context's pinned buffer when it is large enough (a pageable copy is slower)
-        // (words 0-63 of it are left to read_u64 and the status word)
-        uint64_t* dst = ctx && host.size() + 64 <= kPinnedWords ? ctx->h_pinned + 64 : host.data();
-        MQ_TRY(cuda(cudaMemcpyAsync(dst, d_tail, host.size() * 8, cudaMemcpyDeviceToHost, stream), "readback"));
-        if (ctx)
-          MQ_TRY(cuda(cudaMemcpyAsync(ctx->h_pinned + 32, ctx->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                                      stream), "readback"));
-        MQ_TRY(cuda(cudaStreamSynchronize(stream), "cudaStreamSynchronize"));
-        if (dst != host.data()) memcpy(host.data(), dst, host.size() * 8);
-        if (ctx) MQ_TRY(check_status(ctx));
+        MQ_TRY(count_phases());  // its upload zeroes the status word
       }
+      // one read: status word, work counter, row counts and largest counts
+      MQ_TRY(read_tail(2 + 2 * size_t(k)));
       const uint32_t st = uint32_t(host[0]);
       if (st & 1u) {
         // a distinct-key estimate far too low: rebuild every table at two slots per build row
@@ -1745,6 +1934,31 @@ struct BatchJoin {
     return MAPSQ_OK;
   }
 
+  // The one-pass join (count() chose it): lookups, scan, look-back and write
+  // in one launch over the probe tiles, then one read of the row count, which
+  // replaces the capacity in plans[0].T.
+  int write_fused(double bytes) {
+    const JoinPlan& pl = plans[0];
+    const uint64_t ntiles = ceil_div(pl.np, kRowTile), cap = pl.T;
+    uint64_t* lb = nullptr;  // ticket, then one look-back word per tile
+    MQ_TRY(mem->get(1 + ntiles, &lb));
+    MQ_TRY(cuda(cudaMemsetAsync(lb, 0, (1 + ntiles) * sizeof(uint64_t), stream), "memset"));
+    MQ_TRY(upload_descs());  // zeroes the tail: status word and row count
+    const int r = rec(K_FUSED_JOIN);
+    fused_dense_kernel<<<unsigned(ntiles), kThreads, 0, stream>>>(d_descs, lb, status, ctx->wait_spins, cap,
+                                                                 d_tail + 2);
+    launched();
+    done(r, bytes);
+    MQ_TRY(cuda(cudaGetLastError(), "fused_dense_kernel"));
+    MQ_TRY(read_tail(3));
+    const uint32_t st = uint32_t(host[0]);
+    if (st & 2u) return set_error(ctx, MAPSQ_ERR_TIMEOUT, "a bounded look-back wait gave up (status 0x%x)", st);
+    if (st & 4u) return fail(MAPSQ_ERR_UNSUPPORTED, "2048 consecutive probe rows with 2^32 or more matches");
+    if (st) return fail(MAPSQ_ERR_CUDA, "one-pass join: output beyond its capacity");
+    plans[0].T = descs[0].T = host[2];
+    return MAPSQ_OK;
+  }
+
   // Partition and write phases into out[j] (ncols device columns of T rows each).
   int write(uint32_t* const* const* out) {
     std::vector<uint64_t> part(k, 0), wr(k, 0), cr(k, 0), dn(k, 0);
@@ -1771,6 +1985,10 @@ struct BatchJoin {
         }
       }
       if (!pl.T || !pl.lay.ncols || !take[j]) continue;
+      if (fused) {
+        dbytes += 4.0 * pl.lay.nkey * pl.np + 4.0 * pl.np * pl.lay.ncols * pl.maxc + in;  // counted as written in full
+        continue;
+      }
       const uint64_t ntiles = ceil_div(pl.T, kWriteTile);
       if (pl.cross) {
         cr[j] = ntiles;
@@ -1787,6 +2005,7 @@ struct BatchJoin {
         bytes += 4.0 * pl.T * pl.lay.ncols + in;
       }
     }
+    if (fused) return write_fused(dbytes);
     set_items(PH_PART, part);
     set_items(PH_WRITE, wr);
     set_items(PH_CROSS, cr);
@@ -1836,12 +2055,14 @@ int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_ta
   BatchJoin<Scratch> bj{ctx, ctx->stream, ctx->d_status, &scratch};
   bj.algorithm = opts ? opts->algorithm : MAPSQ_JOIN_AUTO;
   bj.tune_from(ctx);
+  bj.allow_fused = true;
   MQ_TRY(bj.prepare(k, L, R));
   MQ_TRY(bj.count());
   std::vector<TableImpl*> tabs(k, nullptr);
   std::vector<uint32_t* const*> cols(k, nullptr);
   int rc = MAPSQ_OK;
   for (uint32_t j = 0; j < k && rc == MAPSQ_OK; ++j) {
+    // (a one-pass join's table is allocated at its capacity, then given its row count)
     rc = table_alloc(ctx, bj.plans[j].T, uint32_t(bj.plans[j].lay.ncols), bj.plans[j].lay.var, &tabs[j]);
     if (rc == MAPSQ_OK) cols[j] = tabs[j]->pub.col;
   }
@@ -1850,6 +2071,7 @@ int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_ta
     for (auto* t : tabs) table_release(ctx, t);
     return rc;
   }
+  if (bj.fused) tabs[0]->pub.nrows = bj.plans[0].T;
   for (uint32_t j = 0; j < k; ++j) out[j] = tabs[j];
   return MAPSQ_OK;
 }

@@ -352,6 +352,48 @@ def test_sorted_count_both_search_modes(ctx):
         out.free()
 
 
+def test_one_pass_dense_join(ctx):
+    """A large probe side against a build side of even key groups takes the
+    one-pass join (lookups, scan, look-back and write in one launch, the output
+    allocated at probe rows x the largest group): exact rows with probe keys
+    that miss, a ragged last tile and the all-ones key, on one and two key
+    columns; a build side with one large group takes the count and write
+    passes, exact too."""
+    r = gen.Rng(79)
+    ctx.set_profiling(True)
+    try:
+        for nkey, groups, n_probe, hot in ((2, 3, (1 << 20) + 777, False), (1, 2, (1 << 21) + 5, False),
+                                           (2, 3, (1 << 20) + 1, True)):
+            ids = np.repeat(np.arange(60_000, dtype=np.uint32), groups)
+            if hot:
+                ids[:5000] = 7  # one group of about 5000 rows: no one-pass bound
+            ids = ids[r.permutation(ids.shape[0])]
+            ids[-1] = 0xFFFFFFFF
+            nb = ids.shape[0]
+            pid = r.below(n_probe, 70_000).astype(np.uint32)  # ids from 60000 on miss
+            pid[:3] = [0xFFFFFFFF, 7, 69_999]
+            if nkey == 2:
+                second = (ids * 3 + 1).astype(np.uint32)
+                second[-1] = 0xFFFFFFFF
+                psecond = (pid * 3 + 1).astype(np.uint32)
+                psecond[0] = 0xFFFFFFFF
+                B = gen.Table([0, 1, 5, 6], [ids, second, r.u32(nb), r.u32(nb)])
+                P = gen.Table([0, 1, 7], [pid, psecond, r.u32(n_probe)])
+            else:
+                B = gen.Table([0, 5], [ids, r.u32(nb)])
+                P = gen.Table([0, 7, 8], [pid, r.u32(n_probe), r.u32(n_probe)])
+            tb, tp = device_table(ctx, B), device_table(ctx, P)
+            before = ctx.kernel_stats().get("fused_join", {}).get("launches", 0)
+            out = ctx.join(tp, tb)
+            used = ctx.kernel_stats().get("fused_join", {}).get("launches", 0) > before
+            assert used == (not hot), (nkey, groups, hot)
+            assert_same_multiset(out, oracle.join_mapreduce(P, B), f"one pass nkey {nkey} hot {hot}")
+            for t in (out, tb, tp):
+                t.free()
+    finally:
+        ctx.set_profiling(False)
+
+
 def test_autotune_sets_ratio_and_joins_stay_exact():
     from paper_1702_03484_gb300 import Context, MapsqError
     with Context(device=0) as c:
