@@ -187,16 +187,17 @@ __device__ __forceinline__ uint64_t* bucket_keys(const HashTable& t, uint32_t b)
 // Group entry {count, begin within the slot tile} of slot s.
 __device__ __forceinline__ uint2* group_of(const HashTable& t, uint32_t s) { return t.group + s; }
 
-// The four keys of a bucket in one 32-byte load (a bucket is 32-byte aligned):
-// read-only through the non-coherent path (probes), or at L2 (inserts, whose
-// buckets other threads fill meanwhile).
-__device__ __forceinline__ void ld_bucket_nc(const uint64_t* p, ulonglong2* k01, ulonglong2* k23) {
+// Four 64-bit words in one 32-byte load (``p`` 32-byte aligned): the keys of a
+// bucket, or four grouped build rows of two values.  Read-only through the
+// non-coherent path (probes, writes), or at L2 (inserts, whose buckets other
+// threads fill meanwhile).
+__device__ __forceinline__ void ld_u64x4_nc(const uint64_t* p, ulonglong2* k01, ulonglong2* k23) {
   asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
                : "=l"(k01->x), "=l"(k01->y), "=l"(k23->x), "=l"(k23->y)
                : "l"(p));
 }
 
-__device__ __forceinline__ void ld_bucket_cg(const uint64_t* p, ulonglong2* k01, ulonglong2* k23) {
+__device__ __forceinline__ void ld_u64x4_cg(const uint64_t* p, ulonglong2* k01, ulonglong2* k23) {
   asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
                : "=l"(k01->x), "=l"(k01->y), "=l"(k23->x), "=l"(k23->y)
                : "l"(p)
@@ -206,7 +207,7 @@ __device__ __forceinline__ void ld_bucket_cg(const uint64_t* p, ulonglong2* k01,
 __device__ __forceinline__ void load_bucket(const HashTable& t, uint64_t key, uint32_t* b, ulonglong2* k01,
                                             ulonglong2* k23) {
   *b = home_bucket(key, t.M);
-  ld_bucket_nc(bucket_keys(t, *b), k01, k23);
+  ld_u64x4_nc(bucket_keys(t, *b), k01, k23);
 }
 
 // Slot of ``key`` in the table, or kNoSlot, starting from its home bucket
@@ -226,7 +227,7 @@ __device__ __forceinline__ uint32_t find_slot(const HashTable& t, uint64_t key, 
       return (hit >> j) & 1u ? b * kBucket + j : kNoSlot;
     }
     b = b + 1 == nbk ? 0 : b + 1;
-    ld_bucket_nc(bucket_keys(t, b), &k01, &k23);
+    ld_u64x4_nc(bucket_keys(t, b), &k01, &k23);
   }
   return kNoSlot;
 }
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 8) hash_insert_kernel(const JoinDesc
         for (uint32_t n = 0; n < nbk && s == kNoSlot; ++n) {
           uint64_t* bkt = bucket_keys(t, b);
           ulonglong2 k01, k23;
-          ld_bucket_cg(bkt, &k01, &k23);
+          ld_u64x4_cg(bkt, &k01, &k23);
           const uint64_t kk[4] = {k01.x, k01.y, k23.x, k23.y};
 #pragma unroll
           for (int q = 0; q < kBucket; ++q) {
@@ -1189,28 +1190,61 @@ __global__ void __launch_bounds__(kThreads, kWriteBlocks) join_write_kernel(cons
   }
 }
 
+// Stores a chunk of four output rows from ``dst`` (j0 of c rows written so
+// far, o the first row's index): one 16-byte store when whole and aligned.
+__device__ __forceinline__ void store_chunk(uint32_t* __restrict__ dst, uint64_t o, uint32_t j0, uint32_t c,
+                                            const uint32_t (&x)[kVec]) {
+  if (j0 + kVec <= c && !((o + j0) & (kVec - 1))) {
+    __stcs(reinterpret_cast<uint4*>(dst + j0), make_uint4(x[0], x[1], x[2], x[3]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < kVec; ++j)
+      if (j0 + j < c) __stcs(dst + j0 + j, x[j]);
+  }
+}
+
 // Output rows [o, o + c) of probe row i, whose key group starts at build row
-// g: every column in chunks of four output rows, one 16-byte store when the
-// chunk is whole and aligned.
+// g: every column in chunks of four output rows.  Two grouped build values per
+// row (a build row's pair is one 8-byte word) come together: four rows' pairs
+// in one 32-byte load when the chunk is whole and 32-byte aligned, else a
+// pair per 8-byte load.
 __device__ __forceinline__ void write_dense_row(const JoinDesc& d, int ncols, uint32_t bstride, uint64_t i, uint64_t o,
                                                 uint32_t c, uint32_t g) {
+  const bool pair = bstride == 2;  // grouped build values, two per row
   for (int col = 0; col < ncols; ++col) {
+    const bool from_build = (d.from_build >> col) & 1u;
+    if (from_build && pair) continue;
     uint32_t* __restrict__ dst = d.out[col] + o;
     const uint32_t* __restrict__ src = d.src[col];
-    const bool from_build = (d.from_build >> col) & 1u;
     const uint32_t pv = from_build ? 0u : __ldg(src + i);
     for (uint32_t j0 = 0; j0 < c; j0 += kVec) {
       uint32_t x[kVec];
 #pragma unroll
       for (int j = 0; j < kVec; ++j)
         x[j] = !from_build ? pv : j0 + j < c ? __ldg(src + uint64_t(g + j0 + j) * bstride) : 0u;
-      if (j0 + kVec <= c && !((o + j0) & (kVec - 1))) {
-        __stcs(reinterpret_cast<uint4*>(dst + j0), make_uint4(x[0], x[1], x[2], x[3]));
+      store_chunk(dst, o, j0, c, x);
+    }
+  }
+  if (pair) {
+    const uint32_t fb = d.from_build;
+    const int c0 = __ffs(fb) - 1, c1 = __ffs(fb & (fb - 1)) - 1;  // the columns of build values 0 and 1
+    const uint64_t* __restrict__ grp = reinterpret_cast<const uint64_t*>(d.grouped);
+    for (uint32_t j0 = 0; j0 < c; j0 += kVec) {
+      const uint32_t r0 = g + j0;
+      ulonglong2 w01 = make_ulonglong2(0ull, 0ull), w23 = make_ulonglong2(0ull, 0ull);
+      if (j0 + kVec <= c && !(r0 & (kVec - 1))) {
+        ld_u64x4_nc(grp + r0, &w01, &w23);
       } else {
-#pragma unroll
-        for (int j = 0; j < kVec; ++j)
-          if (j0 + j < c) __stcs(dst + j0 + j, x[j]);
+        w01.x = __ldg(grp + r0);
+        if (j0 + 1 < c) w01.y = __ldg(grp + r0 + 1);
+        if (j0 + 2 < c) w23.x = __ldg(grp + r0 + 2);
+        if (j0 + 3 < c) w23.y = __ldg(grp + r0 + 3);
       }
+      const uint32_t x0[kVec] = {uint32_t(w01.x), uint32_t(w01.y), uint32_t(w23.x), uint32_t(w23.y)};
+      const uint32_t x1[kVec] = {uint32_t(w01.x >> 32), uint32_t(w01.y >> 32), uint32_t(w23.x >> 32),
+                                 uint32_t(w23.y >> 32)};
+      store_chunk(d.out[c0] + o, o, j0, c, x0);
+      store_chunk(d.out[c1] + o, o, j0, c, x1);
     }
   }
 }
