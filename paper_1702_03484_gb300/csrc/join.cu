@@ -66,7 +66,7 @@ constexpr int kWriteSmem = int(sizeof(uint32_t)) * (2 * kStageRows + 1 + 2 * kMa
 constexpr int kHllBits = 12;
 constexpr int kHllRegs = 1 << kHllBits;
 constexpr uint64_t kHllMinBuild = uint64_t(1) << 16;   // smaller build sides size the table by rows
-constexpr int kHllSpan = 16;                           // row tiles per sketch CTA (one flush per 32K rows)
+constexpr int kHllSpan = 4;                            // row tiles per sketch CTA (one flush per 8K rows)
 constexpr int kBucket = 4;
 constexpr int kPhases = 11;
 constexpr int kDenseUnroll = 4;                        // probe rows of a thread unrolled in the dense write
@@ -82,7 +82,7 @@ constexpr uint32_t kSortedRatio = 4;                   // default: sorted side a
 constexpr int kRegionBits = 8;
 constexpr int kRegions = 1 << kRegionBits;             // build partitions, by the top bits of the home bucket
 constexpr int kHllWords = kHllRegs + kRegions;         // a sketch's registers, then its region histogram
-constexpr int kPartThreads = 512;                      // threads of the partition kernel
+constexpr int kPartThreads = 256;                      // threads of the partition kernel (one per region)
 constexpr int kPartItems = 16;
 constexpr int kPartRows = kPartThreads * kPartItems;   // build rows per partition CTA
 
@@ -275,13 +275,15 @@ __device__ __forceinline__ uint64_t block_scan(uint64_t sum, uint64_t* s_warp, u
 // histogram of the build side's partition.
 __global__ void __launch_bounds__(kThreads) hll_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                       uint32_t k) {
+  constexpr int kHists = kThreads / 32;
   __shared__ uint32_t s[kHllRegs];
-  __shared__ uint32_t s_hist[kRegions];
+  __shared__ uint32_t s_hists[kHists * kRegions];  // one region histogram per warp
+  uint32_t* s_hist = s_hists + (threadIdx.x >> 5) * kRegions;
   const uint32_t j = item_join(first, k, blockIdx.x);
   const JoinDesc& d = jd[j];
   const uint64_t base = (blockIdx.x - first[j]) * uint64_t(kRowTile) * kHllSpan;
   for (int r = threadIdx.x; r < kHllRegs; r += kThreads) s[r] = 0;
-  for (int r = threadIdx.x; r < kRegions; r += kThreads) s_hist[r] = 0;
+  for (int r = threadIdx.x; r < kHists * kRegions; r += kThreads) s_hists[r] = 0;
   __syncthreads();
 #pragma unroll 8
   for (int it = 0; it < kRowItems * kHllSpan; ++it) {
@@ -296,19 +298,27 @@ __global__ void __launch_bounds__(kThreads) hll_kernel(const JoinDesc* __restric
     }
   }
   __syncthreads();
+  // a register already at least this high in global memory stays so (the
+  // maximum only grows): most flushes of a large build side end at the read
   for (int r = threadIdx.x; r < kHllRegs; r += kThreads)
-    if (s[r]) atomicMax(&d.hll[r], s[r]);
-  for (int r = threadIdx.x; r < kRegions; r += kThreads)
-    if (s_hist[r]) atomicAdd(&d.hll[kHllRegs + r], s_hist[r]);
+    if (s[r] && s[r] > __ldcg(d.hll + r)) atomicMax(&d.hll[r], s[r]);
+  for (int r = threadIdx.x; r < kRegions; r += kThreads) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int h = 0; h < kHists; ++h) c += s_hists[h * kRegions + r];
+    if (c) atomicAdd(&d.hll[kHllRegs + r], c);
+  }
 }
 
 // Partition of a large build side by region, so that the insert and the
 // scatter that follow touch the hash table and the grouped values one run of
 // consecutive slots at a time (L2-resident) instead of all over.  A CTA takes
-// kPartRows rows: it ranks every row inside its region (warp-aggregated
-// shared-memory counters), reserves each region's run in the output with one
-// atomic per region, then moves the rows column by column through shared
-// memory so that each region's rows leave as one contiguous run.
+// kPartRows rows: it ranks every row inside its region (shared-memory
+// atomics: the order inside a region is free), reserves each region's run in
+// the output with one atomic per region, notes for every position of its
+// region-ordered buffer the distance to that position's output row, then
+// moves the rows column by column through shared memory so that each region's
+// rows leave as one contiguous run.
 struct PartDesc {
   const uint32_t* src[MAPSQ_MAX_VARS];  // build columns: the key column(s), then the value columns
   uint32_t* dst[MAPSQ_MAX_VARS];        // their partitioned copies
@@ -318,70 +328,75 @@ struct PartDesc {
   uint32_t* check;                      // status word of the checked build's bounds checks
 };
 
-__global__ void __launch_bounds__(kPartThreads, 2) partition_kernel(const PartDesc* __restrict__ pd, const uint64_t* first,
-                                                                uint32_t k) {
-  extern __shared__ __align__(16) uint32_t s_buf[];  // kPartRows values of one column, in region order
-  __shared__ uint8_t s_reg[kPartRows];               // region of each position of s_buf
-  __shared__ uint32_t s_cnt[kRegions], s_lo[kRegions], s_gb[kRegions], s_wsum[kRegions / 32];
+static_assert(kPartThreads == kRegions, "one thread per region in the region scan");
+
+__global__ void __launch_bounds__(kPartThreads, 4) partition_kernel(const PartDesc* __restrict__ pd,
+                                                                    const uint64_t* first, uint32_t k) {
+  __shared__ __align__(16) uint32_t s_buf[kPartRows];  // one column's values, in region order
+  __shared__ uint32_t s_delta[kPartRows];              // global row of position q, minus q (mod 2^32)
+  __shared__ uint32_t s_cnt[kRegions], s_dr[kRegions], s_wsum[kRegions / 32];
   const uint32_t j = item_join(first, k, blockIdx.x);
   const PartDesc& p = pd[j];
   const uint64_t base = (blockIdx.x - first[j]) * uint64_t(kPartRows);
   const uint32_t n = uint32_t(min(uint64_t(kPartRows), p.n - base));
-  const unsigned lane = threadIdx.x & 31;
-  for (int r = threadIdx.x; r < kRegions; r += kPartThreads) s_cnt[r] = 0;
+  const unsigned lane = threadIdx.x & 31, tid = threadIdx.x;
+  s_cnt[tid] = 0;
   __syncthreads();
-  uint32_t pos[kPartItems];  // region << 24 | rank inside the region, then the row's position in s_buf
+  uint32_t pos[kPartItems];  // region << 24 | rank inside the region, then the position in s_buf
 #pragma unroll
-  for (int it = 0; it < kPartItems; ++it) {
-    const uint32_t i = uint32_t(it) * kPartThreads + threadIdx.x;
-    uint32_t reg = kRegions;  // past the end: no region
-    if (i < n) {
-      uint64_t key = __ldg(p.src[0] + base + i);
-      if (p.nkey == 2) key = (key << 32) | __ldg(p.src[1] + base + i);
-      reg = home_region(key);
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, reg);
-    const int leader = __ffs(peers) - 1;
-    uint32_t rb = 0;
-    if (lane == unsigned(leader) && reg < kRegions) rb = atomicAdd(&s_cnt[reg], uint32_t(__popc(peers)));
-    rb = __shfl_sync(0xffffffffu, rb, leader);
-    pos[it] = reg < kRegions ? (reg << 24) | (rb + uint32_t(__popc(peers & ((1u << lane) - 1u)))) : ~0u;
-  }
-  __syncthreads();
-  // exclusive scan of the region counts, and each region's run in the output
-  uint32_t v = 0, inc = 0;
-  if (threadIdx.x < kRegions) {
-    v = inc = s_cnt[threadIdx.x];
+  for (int h = 0; h < kPartItems; h += 8) {
+    uint32_t hi[8], lo[8];
 #pragma unroll
-    for (int dd = 1; dd < 32; dd <<= 1) {
-      const uint32_t x = __shfl_up_sync(0xffffffffu, inc, dd);
-      if (lane >= unsigned(dd)) inc += x;
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t i = uint32_t(h + q) * kPartThreads + tid;
+      hi[q] = i < n ? __ldg(p.src[0] + base + i) : 0u;
+      lo[q] = i < n && p.nkey == 2 ? __ldg(p.src[1] + base + i) : 0u;
     }
-    if (lane == 31) s_wsum[threadIdx.x >> 5] = inc;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t i = uint32_t(h + q) * kPartThreads + tid;
+      if (i < n) {
+        const uint64_t key = p.nkey == 2 ? (uint64_t(hi[q]) << 32) | lo[q] : uint64_t(hi[q]);
+        const uint32_t reg = home_region(key);
+        pos[h + q] = (reg << 24) | atomicAdd(&s_cnt[reg], 1u);
+      } else {
+        pos[h + q] = ~0u;
+      }
+    }
   }
   __syncthreads();
-  if (threadIdx.x < kRegions) {
-    uint32_t before = 0;
-    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) before += s_wsum[w];
-    s_lo[threadIdx.x] = before + inc - v;
-    s_gb[threadIdx.x] = v ? atomicAdd(p.cursor + threadIdx.x, v) : 0u;
+  // exclusive scan of the region counts; each region's run in the output
+  const uint32_t v = s_cnt[tid];
+  uint32_t inc = v;
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, inc, dd);
+    if (lane >= unsigned(dd)) inc += x;
   }
+  if (lane == 31) s_wsum[tid >> 5] = inc;
+  __syncthreads();
+  uint32_t before = 0;
+  for (uint32_t w = 0; w < (tid >> 5); ++w) before += s_wsum[w];
+  const uint32_t lo_r = before + inc - v;
+  const uint32_t gb = v ? atomicAdd(p.cursor + tid, v) : 0u;
+  __syncthreads();  // every thread has read s_cnt
+  s_cnt[tid] = lo_r;
+  s_dr[tid] = gb - lo_r;
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < kPartItems; ++it)
     if (pos[it] != ~0u) {
       const uint32_t reg = pos[it] >> 24;
-      pos[it] = s_lo[reg] + (pos[it] & 0xffffffu);
-      s_reg[pos[it]] = uint8_t(reg);
+      pos[it] = s_cnt[reg] + (pos[it] & 0xffffffu);
+      s_delta[pos[it]] = s_dr[reg];
     }
   for (int c = 0; c < p.ncols; ++c) {
 #pragma unroll
     for (int it = 0; it < kPartItems; ++it)
-      if (pos[it] != ~0u) s_buf[pos[it]] = __ldcs(p.src[c] + base + uint32_t(it) * kPartThreads + threadIdx.x);
+      if (pos[it] != ~0u) s_buf[pos[it]] = __ldcs(p.src[c] + base + uint32_t(it) * kPartThreads + tid);
     __syncthreads();
-    for (uint32_t q = threadIdx.x; q < n; q += kPartThreads) {
-      const uint32_t reg = s_reg[q];
-      const uint64_t at = uint64_t(s_gb[reg]) + (q - s_lo[reg]);
+    for (uint32_t q = tid; q < n; q += kPartThreads) {
+      const uint64_t at = uint32_t(s_delta[q] + q);
       if (MQ_IN_BOUNDS(at < p.n, p.check)) __stcg(p.dst[c] + at, s_buf[q]);
     }
     __syncthreads();
@@ -1789,10 +1804,8 @@ struct BatchJoin {
     MQ_TRY(upload(d_pblob, blob.data(), blob.size()));
     double bytes = 0;
     for (uint32_t j = 0; j < k; ++j) bytes += 8.0 * pdescs[j].ncols * pdescs[j].n;
-    const int smem = 4 * kPartRows;
-    MQ_TRY(set_smem_once(reinterpret_cast<const void*>(partition_kernel), 2, smem));
     const int r = rec(K_PARTITION_BUILD);
-    partition_kernel<<<unsigned(items(PH_REGION)), kPartThreads, smem, stream>>>(
+    partition_kernel<<<unsigned(items(PH_REGION)), kPartThreads, 0, stream>>>(
         reinterpret_cast<const PartDesc*>(d_pblob), phase_first(PH_REGION), k);
     launched();
     done(r, bytes);
