@@ -284,10 +284,18 @@ int store_build(Ctx* ctx, const uint32_t* s, const uint32_t* p, const uint32_t* 
 void store_release(Ctx* ctx);
 
 // Pattern scan (scan.cu).
+enum ScanKind : int32_t {
+  KIND_NONE = 0,    // predicate not in the store: no match
+  KIND_EXIST = 1,   // s and o constant
+  KIND_S_BOUND = 2, // s constant, o variable
+  KIND_O_BOUND = 3, // o constant, s variable
+  KIND_TWO_VARS = 4,
+  KIND_SAME_VAR = 5
+};
 struct PatternRange {
   uint64_t lo, hi;  // row range in the chosen order; hi - lo = matches (before the s==o filter)
   int32_t order;    // 0: SO columns, 1: OS columns, -1: no match
-  int32_t kind;     // see scan.cu
+  int32_t kind;     // a ScanKind
 };
 int validate_pattern(Ctx* ctx, const mapsq_pattern& tp);
 int scan_ranges(Ctx* ctx, const mapsq_pattern* tps, uint32_t n, PatternRange* out);

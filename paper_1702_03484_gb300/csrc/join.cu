@@ -1946,6 +1946,16 @@ struct BatchJoin {
       } else {
         MQ_TRY(count_phases());  // its upload zeroes the status word
       }
+      // cross products and joins with an empty side: every row count is known here
+      bool device_counts = false;
+      for (auto& pl : plans) device_counts |= pl.hash || pl.sorted;
+      if (!device_counts) {
+        for (uint32_t j = 0; j < k; ++j) {
+          plans[j].T = descs[j].T = plans[j].cross ? plans[j].np * plans[j].nb : 0;
+          plans[j].maxc = 0;
+        }
+        return MAPSQ_OK;
+      }
       // one read: status word, work counter, row counts and largest counts
       MQ_TRY(read_tail(2 + 2 * size_t(k)));
       const uint32_t st = uint32_t(host[0]);

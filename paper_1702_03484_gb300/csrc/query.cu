@@ -104,18 +104,51 @@ int query_batch(Ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const u
   std::vector<PatternRange> ranges(all.size());
   MQ_TRY(scan_ranges(ctx, all.data(), uint32_t(all.size()), ranges.data()));
 
+  // A pattern without variables only asks whether its triple is in the
+  // graph, and its range answers: present, it leaves the query (joining a
+  // one-row table without columns changes nothing); absent, the query has no
+  // solution.  A query of such patterns alone keeps them (one row, or none,
+  // without columns).
+  std::vector<std::vector<mapsq_pattern>> qb(nq);
+  std::vector<std::vector<PatternRange>> qr(nq);
+  std::vector<char> none(nq, 0);
+  for (uint32_t q = 0; q < nq; ++q) {
+    bool any_var = false;
+    for (uint32_t i = 0; i < ns[q]; ++i) any_var |= ranges[off[q] + i].kind != KIND_EXIST;
+    for (uint32_t i = 0; i < ns[q]; ++i) {
+      const PatternRange& r = ranges[off[q] + i];
+      if (any_var && r.kind == KIND_EXIST) {
+        none[q] |= r.hi == r.lo;
+        continue;
+      }
+      qb[q].push_back(bgps[q][i]);
+      qr[q].push_back(r);
+    }
+  }
+  // an empty result with every variable of the query, in ascending id
+  auto empty_result = [&](uint32_t q, TableImpl** t) {
+    uint32_t vs = 0;
+    for (uint32_t i = 0; i < ns[q]; ++i) vs |= pattern_var_set(bgps[q][i]);
+    int32_t vars[MAPSQ_MAX_VARS];
+    uint32_t nv = 0;
+    for (int v = 0; v < 32 && nv < MAPSQ_MAX_VARS; ++v)
+      if ((vs >> v) & 1u) vars[nv++] = v;
+    return table_alloc(ctx, 0, nv, vars, t);
+  };
+
   // one query that is a star: its patterns' matches, each sorted on the
   // centre, joined in one round
-  const int32_t centre = nq == 1 ? star_centre(bgps[0], ns[0]) : -1;
+  const int32_t centre = nq == 1 && !none[0] ? star_centre(qb[0].data(), uint32_t(qb[0].size())) : -1;
   if (centre >= 0) {
-    std::vector<TableImpl*> parts(ns[0], nullptr);
+    const uint32_t n = uint32_t(qb[0].size());
+    std::vector<TableImpl*> parts(n, nullptr);
     int rc = MAPSQ_OK;
-    for (uint32_t i = 0; i < ns[0] && rc == MAPSQ_OK; ++i) rc = scan_emit(ctx, bgps[0][i], ranges[i], &parts[i], centre);
+    for (uint32_t i = 0; i < n && rc == MAPSQ_OK; ++i) rc = scan_emit(ctx, qb[0][i], qr[0][i], &parts[i], centre);
     TableImpl* res = nullptr;
     if (rc == MAPSQ_OK) {
       std::vector<const mapsq_table*> tabs;
       for (auto* p : parts) tabs.push_back(&p->pub);
-      rc = join_star(ctx, ns[0], tabs.data(), centre, &res);
+      rc = join_star(ctx, n, tabs.data(), centre, &res);
     }
     for (auto* p : parts) table_release(ctx, p);
     if (rc != MAPSQ_OK) return rc;
@@ -134,14 +167,21 @@ int query_batch(Ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const u
   };
   uint32_t levels = 0;
   for (uint32_t q = 0; q < nq; ++q) {
-    order[q] = plan_order(bgps[q], ns[q], ranges.data() + off[q]);
-    const uint32_t first = order[q][0];
-    const int rc = scan_emit(ctx, bgps[q][first], ranges[off[q] + first], &acc[q]);
+    const int rc = none[q] ? empty_result(q, &acc[q]) : MAPSQ_OK;
     if (rc != MAPSQ_OK) {
       release_all();
       return rc;
     }
-    levels = std::max(levels, ns[q] - 1);
+    if (none[q]) continue;
+    const uint32_t n = uint32_t(qb[q].size());
+    order[q] = plan_order(qb[q].data(), n, qr[q].data());
+    const uint32_t first = order[q][0];
+    const int rc2 = scan_emit(ctx, qb[q][first], qr[q][first], &acc[q]);
+    if (rc2 != MAPSQ_OK) {
+      release_all();
+      return rc2;
+    }
+    levels = std::max(levels, n - 1);
   }
   // level l: the (l+1)-th pattern of every query that has one, joined in one batch
   for (uint32_t l = 1; l <= levels; ++l) {
@@ -150,10 +190,10 @@ int query_batch(Ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const u
     std::vector<const mapsq_table*> L, R;
     int rc = MAPSQ_OK;
     for (uint32_t q = 0; q < nq && rc == MAPSQ_OK; ++q) {
-      if (l >= ns[q]) continue;
+      if (none[q] || l >= qb[q].size()) continue;
       const uint32_t pi = order[q][l];
       TableImpl* part = nullptr;
-      rc = scan_emit(ctx, bgps[q][pi], ranges[off[q] + pi], &part, shared_var(acc[q]->pub, bgps[q][pi]));
+      rc = scan_emit(ctx, qb[q][pi], qr[q][pi], &part, shared_var(acc[q]->pub, qb[q][pi]));
       if (rc != MAPSQ_OK) break;
       who.push_back(q);
       parts.push_back(part);

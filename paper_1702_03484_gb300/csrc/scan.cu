@@ -17,15 +17,6 @@ namespace mapsq {
 
 namespace {
 
-enum ScanKind : int32_t {
-  KIND_NONE = 0,    // predicate not in the store: no match
-  KIND_EXIST = 1,   // s and o constant
-  KIND_S_BOUND = 2, // s constant, o variable
-  KIND_O_BOUND = 3, // o constant, s variable
-  KIND_TWO_VARS = 4,
-  KIND_SAME_VAR = 5
-};
-
 struct RangeQuery {
   uint64_t b, e;     // predicate segment
   uint32_t v0, v1;   // constants

@@ -157,6 +157,31 @@ def test_query_batch_matches_oracle(ctx, small_graph):
     assert ctx.query_batch([]) == []
 
 
+def test_query_patterns_without_variables(ctx, small_graph):
+    """A pattern without variables tests one triple's presence: a present one
+    changes nothing, an absent one empties the BGP; BGPs of such patterns
+    alone give one row without columns, or none.  Plain and batched, stars
+    and chains, against the oracle."""
+    s, p, o = small_graph
+    ctx.load_triples(s, p, o)
+    G = oracle.distinct_triples(s, p, o)
+    here = (int(s[7]), int(p[7]), int(o[7]), 0)
+    absent = (int(s[7]), int(p[7]), 0xFFFFFFF0, 0)
+    bgps = generate_bgps(GraphIndex(s, p, o), 6, seed=23)
+    cases = []
+    for b in bgps:
+        pats = list(b["patterns"])
+        cases += [pats + [here], [here] + pats, pats + [absent], [here, absent] + pats]
+    cases += [[here], [here, here], [absent], [here, absent], [absent, here]]
+    for bgp in cases:
+        res = ctx.query(bgp)
+        assert_same_multiset(res, oracle.evaluate_bgp(G, bgp, is_set=True), str(bgp))
+        res.free()
+    for bgp, r in zip(cases, ctx.query_batch(cases)):
+        assert_same_multiset(r, oracle.evaluate_bgp(G, bgp, is_set=True), "batched " + str(bgp))
+        r.free()
+
+
 def test_query_order_invariance(ctx, small_graph):
     s, p, o = small_graph
     ctx.load_triples(s, p, o)
