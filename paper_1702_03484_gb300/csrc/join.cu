@@ -1646,8 +1646,9 @@ struct BatchJoin {
         if (!plans[j].hll) continue;
         const uint32_t* w = reinterpret_cast<const uint32_t*>(host.data()) + size_t(h++) * kHllWords;
         const double est = hll_estimate(w);
-        // load factor about 0.6
-        plans[j].M = std::min<uint64_t>(plans[j].M, std::max<uint64_t>(1024, uint64_t(1.6 * est) + 1024));
+        // load factor about 0.4 (measured: 0.8 and 0.6 probe past the home
+        // bucket more often, 0.3 only grows the table)
+        plans[j].M = std::min<uint64_t>(plans[j].M, std::max<uint64_t>(1024, uint64_t(2.5 * est) + 1024));
         // the partition's region offsets (exclusive prefix sums of the histogram)
         plans[j].region_off.assign(kRegions, 0);
         uint32_t run = 0;
