@@ -56,9 +56,11 @@ constexpr int kWriteTile = kThreads * kWriteRows;      // output rows per write 
 constexpr int kStageRows = 1800;                       // probe rows per stage chunk
 constexpr int kWriteBlocks = 4;                        // write CTAs per SM (register budget)
 constexpr int kStageChunks = 4;                        // stage chunks at most per write tile
-constexpr int kProbeIn = 2;                            // probe rows in flight per thread
-constexpr int kProbeBlocks = 5;                        // probe CTAs per SM (register budget)
-constexpr int kFusedBlocks = 6;                        // one-pass dense join CTAs per SM (register budget)
+constexpr int kProbeIn = 1;                            // probe rows in flight per thread (registers go to occupancy)
+constexpr int kProbeBlocks = 8;                        // probe CTAs per SM (32 registers)
+constexpr int kDenseBlocks = 8;                        // dense write CTAs per SM (32 registers)
+constexpr int kFusedBlocks = 8;                        // one-pass dense join CTAs per SM (32 registers)
+constexpr int kFusedProbeIn = 1;                       // its lookups in flight per thread (registers go to occupancy)
 constexpr uint64_t kFusedMinProbe = uint64_t(1) << 20;  // probe sides from which a dense join may take one pass
 constexpr int kEarlyTiles = 64;                        // joins of up to this many write tiles are partitioned by the count scan
 constexpr int kMapWords = kWriteTile + kWriteTile / 32;  // row map, padded one word per 32
@@ -682,20 +684,17 @@ __global__ void __launch_bounds__(kThreads, kProbeBlocks) probe_count_kernel(con
   const uint64_t base = tile * kRowTile;
   const uint64_t np = d.np;
   auto pad = [](int i) { return i + (i >> 5); };
-  // every key of the thread's rows first: the streamed loads overlap the lookups
-  uint64_t keys[kRowItems];
-#pragma unroll
-  for (int q = 0; q < kRowItems; ++q) {
-    const uint64_t row = base + uint64_t(q) * kThreads + threadIdx.x;
-    keys[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
-  }
+  // keys loaded as they are needed: the registers go to more CTAs per SM
 #pragma unroll
   for (int h0 = 0; h0 < kRowItems; h0 += kProbeIn) {
     uint64_t key[kProbeIn];
     uint32_t b[kProbeIn], s[kProbeIn];
     ulonglong2 k01[kProbeIn], k23[kProbeIn];
 #pragma unroll
-    for (int q = 0; q < kProbeIn; ++q) key[q] = keys[h0 + q];
+    for (int q = 0; q < kProbeIn; ++q) {
+      const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
+      key[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
+    }
 #pragma unroll
     for (int q = 0; q < kProbeIn; ++q)
       if (key[q] != kEmptyKey) load_bucket(t, key[q], &b[q], &k01[q], &k23[q]);
@@ -1271,7 +1270,7 @@ __device__ __forceinline__ void write_dense_row(const JoinDesc& d, int ncols, ui
 // stores of a column stay within a few lines; every whole aligned run of four
 // output rows takes one 16-byte store per column.  No partition, no shared
 // memory, no barrier.
-__global__ void __launch_bounds__(kThreads) dense_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
+__global__ void __launch_bounds__(kThreads, kDenseBlocks) dense_write_kernel(const JoinDesc* __restrict__ jd, const uint64_t* first,
                                                               uint32_t k) {
   const uint32_t jj = item_join(first, k, blockIdx.x);
   const JoinDesc& d = jd[jj];
@@ -1324,28 +1323,28 @@ __global__ void __launch_bounds__(kThreads, kFusedBlocks) fused_dense_kernel(con
   const uint32_t tile = s_tile;
   const uint64_t base = uint64_t(tile) * kRowTile, np = d.np;
   if (base >= np) return;  // the same for the whole block
-  // lookups, kProbeIn rows in flight per thread (keys loaded as they are
+  // lookups, kFusedProbeIn rows in flight per thread (keys loaded as they are
   // needed: the registers go to more CTAs per SM)
 #pragma unroll
-  for (int h0 = 0; h0 < kRowItems; h0 += kProbeIn) {
-    uint64_t key[kProbeIn];
-    uint32_t b[kProbeIn], sl[kProbeIn];
-    ulonglong2 k01[kProbeIn], k23[kProbeIn];
+  for (int h0 = 0; h0 < kRowItems; h0 += kFusedProbeIn) {
+    uint64_t key[kFusedProbeIn];
+    uint32_t b[kFusedProbeIn], sl[kFusedProbeIn];
+    ulonglong2 k01[kFusedProbeIn], k23[kFusedProbeIn];
 #pragma unroll
-    for (int q = 0; q < kProbeIn; ++q) {
+    for (int q = 0; q < kFusedProbeIn; ++q) {
       const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
       key[q] = row < np ? load_key(d.pk, row) : kEmptyKey;
     }
 #pragma unroll
-    for (int q = 0; q < kProbeIn; ++q)
+    for (int q = 0; q < kFusedProbeIn; ++q)
       if (key[q] != kEmptyKey) load_bucket(t, key[q], &b[q], &k01[q], &k23[q]);
 #pragma unroll
-    for (int q = 0; q < kProbeIn; ++q) {
+    for (int q = 0; q < kFusedProbeIn; ++q) {
       const uint64_t row = base + uint64_t(h0 + q) * kThreads + threadIdx.x;
       sl[q] = row < np ? find_slot(t, key[q], b[q], k01[q], k23[q]) : kNoSlot;
     }
 #pragma unroll
-    for (int q = 0; q < kProbeIn; ++q) {
+    for (int q = 0; q < kFusedProbeIn; ++q) {
       const int loc = (h0 + q) * kThreads + threadIdx.x;
       const uint2 g = sl[q] != kNoSlot ? *group_of(t, sl[q]) : make_uint2(0u, 0u);
       s_beg[loc] = g.x ? group_begin(t, sl[q], g.y) : 0u;
