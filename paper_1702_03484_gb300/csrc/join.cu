@@ -33,6 +33,7 @@
 // table's other columns, then the right table's.  No shared variable: the cross
 // product, one key group holding every row.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -406,12 +407,20 @@ __global__ void __launch_bounds__(kPartThreads, 4) partition_kernel(const PartDe
 }
 
 double hll_estimate(const uint32_t* regs) {
+  // 2^-r for every register value (at most 64 - kHllBits + 1): a table, since
+  // a batch sizes up to hundreds of tables one after another on the host
+  static const std::array<double, 65> inv = [] {
+    std::array<double, 65> a{};
+    for (int r = 0; r <= 64; ++r) a[r] = std::ldexp(1.0, -r);
+    return a;
+  }();
   const double m = kHllRegs;
   double sum = 0.0;
   int zeros = 0;
   for (int j = 0; j < kHllRegs; ++j) {
-    sum += std::ldexp(1.0, -int(regs[j]));
-    zeros += regs[j] == 0;
+    const uint32_t r = regs[j] < 64u ? regs[j] : 64u;
+    sum += inv[r];
+    zeros += r == 0;
   }
   double e = (0.7213 / (1.0 + 1.079 / m)) * m * m / sum;
   if (e <= 2.5 * m && zeros > 0) e = m * std::log(m / zeros);  // small-range correction (linear counting)
