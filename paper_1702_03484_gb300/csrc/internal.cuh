@@ -204,6 +204,19 @@ struct Scratch {
   // (the interface matches the fixed-array carver, which reuses its space).
   size_t mark() const { return 0; }
   void rewind(size_t) {}
+  // One block for the requests that follow (a batch's per-join arrays), so
+  // that they cost one device allocation instead of one each.  A hint: if the
+  // block cannot be had, each request allocates as before.
+  int reserve(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes <= left || bytes <= kChunk) return MAPSQ_OK;
+    void* p = nullptr;
+    if (dev_alloc(ctx, bytes, &p) != MAPSQ_OK) return MAPSQ_OK;
+    blocks.push_back({p, bytes});
+    cur = static_cast<char*>(p);
+    left = bytes;
+    return MAPSQ_OK;
+  }
   template <class T>
   int get(size_t count, T** out) {
     size_t bytes = count * sizeof(T);

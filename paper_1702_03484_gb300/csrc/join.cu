@@ -1719,6 +1719,20 @@ struct BatchJoin {
     if (keys) MQ_TRY(cuda(cudaMemsetAsync(all_keys, 0xff, keys * 8, stream), "memset"));  // all slots empty
     if (groups) MQ_TRY(cuda(cudaMemsetAsync(all_groups, 0, groups * 8, stream), "memset"));
     std::vector<uint64_t> ins(k, 0), slots(k, 0), scat(k, 0), cnt(k, 0), scnt(k, 0);
+    // the per-join arrays below, in one block (as the allocator rounds them)
+    size_t need = 0;
+    auto add = [&need](uint64_t count, size_t elem) { need += ((count * elem ? count * elem : 16) + 255) & ~size_t(255); };
+    for (uint32_t j = 0; j < k; ++j) {
+      const JoinPlan& pl = plans[j];
+      if (!pl.sorted && !pl.hash) continue;
+      const uint64_t nt = ceil_div(pl.np, kRowTile);
+      add(kEarlyTiles + 1, 8), add(pl.np / 32 + 1, 4), add(pl.np, 4), add(pl.np, 4), add(nt, 8), add(nt + 1, 8);
+      if (pl.sorted) continue;
+      const uint64_t nslot_tiles = ceil_div(pl.M + 1, kRowTile);
+      add(nslot_tiles, 8), add(nslot_tiles + 1, 8), add(pl.nb, 4), add(pl.nb, 4);
+      if (descs[j].nbv) add(pl.nb * descs[j].nbv, 4);
+    }
+    MQ_TRY(mem->reserve(need));
     size_t ko = 0, go = 0;
     for (uint32_t j = 0; j < k; ++j) {
       const JoinPlan& pl = plans[j];
@@ -2323,6 +2337,7 @@ int noalloc_scratch(unsigned char** out) {
 struct Carve {
   unsigned char* base;
   size_t used = 0;
+  int reserve(size_t) { return MAPSQ_OK; }  // one fixed array: nothing to reserve
   size_t mark() const { return used; }
   void rewind(size_t m) { used = m; }  // the stream has finished with everything past m
   template <class T>
