@@ -317,7 +317,9 @@ MAPSQ_API int mapsq_join_star(mapsq_ctx* ctx, uint32_t k, const mapsq_table* con
  * one launch for the whole batch, the write phase a persistent kernel fed by a
  * device work queue, and the batch synchronises once to size all outputs
  * (twice with large hash build sides, as mapsq_join), so many small joins cost
- * about as much as one.  out[j] receives join j's table.
+ * about as much as one.  out[j] receives join j's table.  With k > 1 the k
+ * tables share one device allocation: each is freed with mapsq_table_free as
+ * usual, and their memory returns when the last of them is freed.
  * Errors: as mapsq_join (then no table is returned). */
 MAPSQ_API int mapsq_join_batch(mapsq_ctx* ctx, uint32_t k, const mapsq_table* const* left,
                                const mapsq_table* const* right, mapsq_table** out, const mapsq_join_opts* opts);
@@ -336,7 +338,10 @@ MAPSQ_API int mapsq_query(mapsq_ctx* ctx, const mapsq_pattern* bgp, uint32_t n, 
  * evaluated together.  Their range searches are one launch; at each level,
  * every query's next join goes into one batched join (mapsq_join_batch), so
  * the batch synchronises about once per level instead of once per join.
- * out[q] receives query q's result (columns in ascending variable id).
+ * out[q] receives query q's result (columns in ascending variable id).  The
+ * results of the queries whose last join falls in the same level share one
+ * device allocation with that level's other results (as mapsq_join_batch's),
+ * returned when the last of them is freed.
  * All or nothing: on error no table is returned.  Errors: as mapsq_query. */
 MAPSQ_API int mapsq_query_batch(mapsq_ctx* ctx, uint32_t nq, const mapsq_pattern* const* bgps, const uint32_t* n,
                                 mapsq_table** out);

@@ -116,6 +116,57 @@ int table_view(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, uin
   return MAPSQ_OK;
 }
 
+// The result tables of a batch in one device allocation: each table is a
+// view of its part (columns 256-byte aligned, as table_alloc lays them out),
+// and the block goes when the last of the tables is released.
+int tables_alloc_shared(Ctx* ctx, uint32_t k, const uint64_t* nrows, const uint32_t* ncols,
+                        const int32_t* const* var, TableImpl** out) {
+  std::vector<size_t> off(k, 0), stride(k, 0);
+  size_t total = 0;
+  for (uint32_t j = 0; j < k; ++j) {
+    if (ncols[j] > MAPSQ_MAX_VARS) return set_error(ctx, MAPSQ_ERR_INVALID, "table with %u columns", ncols[j]);
+    stride[j] = size_t((nrows[j] + 63) & ~uint64_t(63));
+    off[j] = total;
+    total += (stride[j] * ncols[j] * sizeof(uint32_t) + 255) & ~size_t(255);
+  }
+  if (total == 0) {  // no columns or no rows anywhere: nothing to share
+    for (uint32_t j = 0; j < k; ++j) {
+      const int rc = table_alloc(ctx, nrows[j], ncols[j], var[j], &out[j]);
+      if (rc != MAPSQ_OK) {
+        for (uint32_t i = 0; i < j; ++i) table_release(ctx, out[i]);
+        return rc;
+      }
+    }
+    return MAPSQ_OK;
+  }
+  SharedBlock* b = new (std::nothrow) SharedBlock();
+  if (!b) return set_error(ctx, MAPSQ_ERR_OOM, "host allocation failed");
+  int rc = dev_alloc(ctx, total, &b->ptr);
+  if (rc != MAPSQ_OK) {
+    delete b;
+    return rc;
+  }
+  b->bytes = total;
+  uint32_t made = 0;
+  for (; made < k && rc == MAPSQ_OK; ++made) {
+    uint32_t* cols[MAPSQ_MAX_VARS] = {};
+    for (uint32_t c = 0; c < ncols[made]; ++c)
+      cols[c] = reinterpret_cast<uint32_t*>(static_cast<char*>(b->ptr) + off[made]) + stride[made] * c;
+    rc = table_view(ctx, nrows[made], ncols[made], var[made], cols, b, &out[made]);
+    if (rc == MAPSQ_OK) out[made]->bytes = stride[made] * ncols[made] * sizeof(uint32_t);
+    else break;
+  }
+  if (rc != MAPSQ_OK) {
+    if (made == 0) {
+      dev_free(ctx, b->ptr, b->bytes);
+      delete b;
+    }
+    for (uint32_t i = 0; i < made; ++i) table_release(ctx, out[i]);  // the last one frees the block
+    return rc;
+  }
+  return MAPSQ_OK;
+}
+
 void shared_release(Ctx* ctx, SharedBlock* b) {
   if (!b || --b->refs > 0) return;
   dev_free(ctx, b->ptr, b->bytes);

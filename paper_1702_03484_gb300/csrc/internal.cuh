@@ -251,6 +251,8 @@ int table_view(Ctx* ctx, uint64_t nrows, uint32_t ncols, const int32_t* var, uin
                SharedBlock* owner, TableImpl** out);
 void table_release(Ctx* ctx, TableImpl* t);
 void shared_release(Ctx* ctx, SharedBlock* b);
+int tables_alloc_shared(Ctx* ctx, uint32_t k, const uint64_t* nrows, const uint32_t* ncols,
+                        const int32_t* const* var, TableImpl** out);
 
 // Profiling brackets around one launch (no-ops while profiling is off).
 int prof_begin(Ctx* ctx, int kid);

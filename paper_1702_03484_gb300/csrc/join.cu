@@ -2141,10 +2141,22 @@ int join_batch(Ctx* ctx, uint32_t k, const mapsq_table* const* L, const mapsq_ta
   std::vector<TableImpl*> tabs(k, nullptr);
   std::vector<uint32_t* const*> cols(k, nullptr);
   int rc = MAPSQ_OK;
-  for (uint32_t j = 0; j < k && rc == MAPSQ_OK; ++j) {
+  if (k > 1) {
+    // the batch's results in one allocation (each table a view of its part)
+    std::vector<uint64_t> rows(k);
+    std::vector<uint32_t> nc(k);
+    std::vector<const int32_t*> vars(k);
+    for (uint32_t j = 0; j < k; ++j) {
+      rows[j] = bj.plans[j].T;
+      nc[j] = uint32_t(bj.plans[j].lay.ncols);
+      vars[j] = bj.plans[j].lay.var;
+    }
+    rc = tables_alloc_shared(ctx, k, rows.data(), nc.data(), vars.data(), tabs.data());
+    for (uint32_t j = 0; j < k && rc == MAPSQ_OK; ++j) cols[j] = tabs[j]->pub.col;
+  } else {
     // (a one-pass join's table is allocated at its capacity, then given its row count)
-    rc = table_alloc(ctx, bj.plans[j].T, uint32_t(bj.plans[j].lay.ncols), bj.plans[j].lay.var, &tabs[j]);
-    if (rc == MAPSQ_OK) cols[j] = tabs[j]->pub.col;
+    rc = table_alloc(ctx, bj.plans[0].T, uint32_t(bj.plans[0].lay.ncols), bj.plans[0].lay.var, &tabs[0]);
+    if (rc == MAPSQ_OK) cols[0] = tabs[0]->pub.col;
   }
   if (rc == MAPSQ_OK) rc = bj.write(cols.data());
   if (rc != MAPSQ_OK) {
