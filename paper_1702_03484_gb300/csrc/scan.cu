@@ -53,6 +53,17 @@ __device__ __forceinline__ uint64_t warp_bound(const uint32_t* a, uint64_t lo, u
   return lo + __popc(__ballot_sync(0xffffffffu, below));
 }
 
+// The end of the run of v that starts at lo (the first index > v from lo
+// on): most runs (a subject's objects under one predicate, an object's
+// subjects) are short, so the 32 positions after lo are tested first, one
+// dependent load; a longer run is then searched as above.
+__device__ __forceinline__ uint64_t warp_run_end(const uint32_t* a, uint64_t lo, uint64_t hi, uint32_t v) {
+  const uint64_t pos = lo + (threadIdx.x & 31);
+  const unsigned in = __ballot_sync(0xffffffffu, pos < hi && a[pos] <= v);  // a prefix of the lanes
+  if (in != 0xffffffffu) return lo + __popc(in);
+  return warp_bound(a, lo + 32, hi, v, true);
+}
+
 // One warp per pattern.
 __global__ void scan_ranges_kernel(const RangeQuery* __restrict__ q, uint32_t n, StoreCols st,
                                    uint64_t* __restrict__ out) {
@@ -63,15 +74,15 @@ __global__ void scan_ranges_kernel(const RangeQuery* __restrict__ q, uint32_t n,
   switch (r.kind) {
     case KIND_S_BOUND:
       lo = warp_bound(st.so_s, r.b, r.e, r.v0, false);
-      hi = warp_bound(st.so_s, lo, r.e, r.v0, true);
+      hi = warp_run_end(st.so_s, lo, r.e, r.v0);
       break;
     case KIND_O_BOUND:
       lo = warp_bound(st.os_o, r.b, r.e, r.v1, false);
-      hi = warp_bound(st.os_o, lo, r.e, r.v1, true);
+      hi = warp_run_end(st.os_o, lo, r.e, r.v1);
       break;
     case KIND_EXIST: {
       uint64_t a = warp_bound(st.so_s, r.b, r.e, r.v0, false);
-      uint64_t z = warp_bound(st.so_s, a, r.e, r.v0, true);
+      uint64_t z = warp_run_end(st.so_s, a, r.e, r.v0);
       uint64_t k = warp_bound(st.so_o, a, z, r.v1, false);
       lo = k;
       hi = (k < z && st.so_o[k] == r.v1) ? k + 1 : k;
