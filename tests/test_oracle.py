@@ -318,6 +318,30 @@ def tiny_bgp(seed, n_terms=10, n_pred=3, max_vars=4):
     return bgp
 
 
+def test_patterns_without_variables_brute_force():
+    """A pattern with no variable holds under every assignment or under none:
+    present, the BGP's solutions are those of the other patterns; absent,
+    there are none (with every variable of the BGP); alone, one row without
+    columns or none.  Checked against brute-force enumeration."""
+    for seed in range(40):
+        graph = tiny_graph(seed)
+        s, p, o = graph
+        here = (int(s[0]), int(p[0]), int(o[0]), 0)
+        triples = set(zip(s.tolist(), p.tolist(), o.tolist()))
+        gone = next((a, int(p[0]), b, 0) for a in range(12) for b in range(12) if (a, int(p[0]), b) not in triples)
+        rest = [tp for tp in tiny_bgp(seed) if tp[3]] or [(0, int(p[1]), 1, 5)]
+        base = multiset(oracle.brute_force_bgp(graph, rest))
+        assert multiset(oracle.brute_force_bgp(graph, rest + [here])) == base
+        none = multiset(oracle.brute_force_bgp(graph, [gone] + rest))
+        assert none == (base[0], [])
+        assert multiset(oracle.brute_force_bgp(graph, [here])) == ([], [()])
+        assert multiset(oracle.brute_force_bgp(graph, [here, gone])) == ([], [])
+        for bgp in (rest + [here], [gone] + rest, [here], [here, gone]):
+            want = multiset(oracle.brute_force_bgp(graph, bgp))
+            for join in JOINS:
+                assert multiset(oracle.evaluate_bgp(graph, bgp, join=join)) == want, (seed, bgp)
+
+
 def test_bgp_matches_brute_force():
     for seed in range(60):
         graph = tiny_graph(seed)
