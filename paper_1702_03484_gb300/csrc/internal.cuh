@@ -211,7 +211,11 @@ struct Scratch {
     bytes = (bytes + 255) & ~size_t(255);
     if (bytes <= left || bytes <= kChunk) return MAPSQ_OK;
     void* p = nullptr;
-    if (dev_alloc(ctx, bytes, &p) != MAPSQ_OK) return MAPSQ_OK;
+    const std::string before = ctx->err;
+    if (dev_alloc(ctx, bytes, &p) != MAPSQ_OK) {
+      ctx->err = before;  // not an error of the call: its requests allocate one by one
+      return MAPSQ_OK;
+    }
     blocks.push_back({p, bytes});
     cur = static_cast<char*>(p);
     left = bytes;
